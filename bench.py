@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Benchmark of the finite-frequency traveltime tomography hot path on GB300.
+
+Workload (default ``ring256``): 256 transducers on a 100 mm ring (32640 pairs), Gaussian
+spectrum 1 MHz / 0.4 MHz, 4096-sample Phi table to 3 us, 200 x 200 x 40 voxels at 1 mm,
+three nested cylinders, data = J dc + N(0, 5 ns), 30 CGLS iterations with relative damping
+1e-3. Synthetic, seeded inputs (the paper's lab dataset is not available).
+
+One step = one damped least-squares solve (fft_cg_solve, 30 iterations) on resident data:
+(30 + 1) applications each of J and J^T, every entry rebuilt on the fly. The Phi table and
+the culled geometry are built once before timing (their build time is reported as
+``setup_ms``). The metric is in-support pair-voxel evaluations per second (J and J^T
+together); the roofline is that of the J^T kernel against the FP32 issue rate of the chip.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+Under torchrun each rank runs its own replica (the path has no exchange step on one
+acquisition per GPU); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "J & J^T pair-voxel evals/s (in-support), ms per CG iter, % FP32 roofline, err vs FP64 oracle"
+UNIT = "eval/s"
+# FP32 lane operations of one in-support evaluation in the canonical (textbook detour) count:
+# 6 FADD (difference vectors), 6 (squared norms), 2 (R = R^2 rsqrt), 3 (scaled detour),
+# 2 (index, fraction), 2 (lerp), 1 (rsqrt product), 1 (times Phi), 1 (accumulate).
+OPS_PER_EVAL = 24
+FP32_LANES_PER_SM_CLK = 128
+# DRAM bytes (read + write) of one J^T apply-kernel launch on this workload, from the ncu
+# capture summarised in profiles/apply_kernel_ring256.md; None until captured for the
+# current kernel.
+APPLY_TRAFFIC_BYTES = None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- CPU oracle legs
+
+def oracle_sample_rate(w, n_rows: int, seed: int = 0):
+    """FP64 oracle J on a random row sample: (in-support evals/s, seconds, rows, threads)."""
+    import oracle
+    og = oracle.Geometry.from_workload(w)
+    rows = np.sort(np.random.default_rng(seed).choice(og.M, n_rows, replace=False)).astype(np.int64)
+    units = og.count_support(rows)
+    m = wl.model_for(w)
+    t0 = time.perf_counter()
+    og.J(m, rows)
+    dt = time.perf_counter() - t0
+    return units / dt, dt, units, oracle.n_threads()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    w = wl.by_name(args.workload)
+    og = oracle.Geometry.from_workload(w)
+    m = wl.model_for(w)
+    rng = np.random.default_rng(123)
+    n_rows = args.ref_rows
+    samples = [np.sort(rng.choice(og.M, n_rows, replace=False)).astype(np.int64)
+               for _ in range(args.warmup + args.steps)]
+    units = [og.count_support(r) for r in samples]
+    times = []
+    for i, rows in enumerate(samples):
+        t0 = time.perf_counter()
+        og.J(m, rows)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append((dt, units[i]))
+    tot_t = sum(t for t, _ in times)
+    tot_u = sum(u for _, u in times)
+    value = tot_u / tot_t
+    sample = f"FP64 oracle J on {n_rows} random rows of {w.name} per step ({tot_u // max(len(times), 1)} in-support evals)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded ring-array workload)",
+        "config": {"workload": w.name, "pairs": og.M, "voxels": og.V, "l2": "inputs resident, CPU"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.n_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="ring256", choices=["ring32", "ring256"])
+    ap.add_argument("--dt-mode", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-rows", type=int, default=1024)
+    ap.add_argument("--cpu-rows", type=int, default=4096)
+    args = ap.parse_args()
+
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    import paper_1908_03302_gb300 as fg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = wl.by_name(args.workload)
+    band = w.bands[0]
+
+    # ---- setup (not part of a step): table, geometry, data
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    table = fg.Table(band.f_center_hz, band.f_sigma_hz, band.n_samples, band.dt_max)
+    t1 = time.perf_counter()
+    geo = fg.Geometry(w.tx, w.row_pairs(), w.grid, w.c0, [table], dt_mode=args.dt_mode)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    info = geo.info()
+    support = int(info.support_evals)
+    m_true = torch.as_tensor(wl.model_for(w), dtype=torch.float32, device=dev)
+    noise = torch.as_tensor(wl.noise(geo.M, w.noise_seed), dtype=torch.float32, device=dev)
+    d = geo.J(m_true) + noise
+    m = torch.zeros(geo.V, dtype=torch.float32, device=dev)
+    geo.frob2()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    n_iter = w.cg_iters
+    evals_per_step = 2 * (n_iter + 1) * support
+    launches_per_step = 8 + 10 * n_iter
+
+    def step(mbuf):
+        mbuf.zero_()
+        geo.cg_solve(d, w.lambda_rel, n_iter, m=mbuf)
+
+    for _ in range(args.warmup):
+        step(m)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step(m)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(sum(step_ms), ws)
+
+    # ---- dominant kernel: J^T (and J) applications timed alone on the launching stream
+    reps = 10
+    r = torch.randn(geo.M, device=dev, dtype=torch.float32) * 1e-8
+    gbuf = torch.empty(geo.V, device=dev, dtype=torch.float32)
+    dbuf = torch.empty(geo.M, device=dev, dtype=torch.float32)
+    jt_ms, j_ms = [], []
+    for i in range(reps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        geo.JT(r, out=gbuf)
+        b.record(stream)
+        c, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.record(stream)
+        geo.J(m_true, out=dbuf)
+        e.record(stream)
+        torch.cuda.synchronize()
+        jt_ms.append(a.elapsed_time(b))
+        j_ms.append(c.elapsed_time(e))
+    clocks = sampler.stop()
+
+    # ---- end to end through the public API with host buffers
+    d_host = d.cpu().pin_memory()
+    m_host = torch.empty(geo.V, dtype=torch.float32).pin_memory()
+    d_dev = torch.empty_like(d)
+    m_dev = torch.empty_like(m)
+    e2e_ms = []
+    for i in range(max(2, min(args.steps, 5))):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t_a = time.perf_counter()
+        d_dev.copy_(d_host, non_blocking=True)
+        m_dev.zero_()
+        geo.cg_solve(d_dev, w.lambda_rel, n_iter, m=m_dev)
+        m_host.copy_(m_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t_a))
+    e2e_total = max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws)
+
+    # ---- parity against the FP64 oracle on sampled rows and voxels (rank 0)
+    err = None
+    cpu = None
+    if rank == 0:
+        import oracle
+        og = oracle.Geometry.from_workload(w)
+        rng = np.random.default_rng(99)
+        rows = np.sort(rng.choice(og.M, 128, replace=False)).astype(np.int64)
+        vox = np.sort(rng.choice(og.V, 1024, replace=False)).astype(np.int64)
+        m_np = wl.model_for(w)
+        dj = geo.J(m_true).double().cpu().numpy()[rows]
+        dj_ref = og.J(m_np, rows)
+        rr = r.double().cpu().numpy()
+        gj = geo.JT(r).double().cpu().numpy()[vox]
+        gj_ref = og.JT(rr, vox)
+        err = {"J_rel_l2": float(np.linalg.norm(dj - dj_ref) / np.linalg.norm(dj_ref)),
+               "JT_rel_l2": float(np.linalg.norm(gj - gj_ref) / np.linalg.norm(gj_ref)),
+               "sample": "J on 128 random rows, J^T on 1024 random voxels"}
+        if not args.no_cpu_baseline:
+            rate, secs, units, threads = oracle_sample_rate(w, args.cpu_rows)
+            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": f"FP64 oracle J on {args.cpu_rows} random rows of {w.name} "
+                             f"({units} in-support evals, {secs:.1f} s)"}
+
+    if rank != 0:
+        return 0
+    pk, pk_kind = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    sm_max = float(pk.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    peak_evals = sm_count * FP32_LANES_PER_SM_CLK * sm_max * 1e6 / OPS_PER_EVAL
+    jt_avg = statistics.mean(jt_ms) * 1e-3
+    j_avg = statistics.mean(j_ms) * 1e-3
+    achieved = support / jt_avg
+    value = ws * evals_per_step * args.steps / (total_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded ring-array workload; FP32 kernels, FP64 CG scalars)",
+        "config": {"workload": w.name, "pairs": geo.M, "voxels": geo.V, "cg_iters": n_iter,
+                   "support_evals_per_apply": support, "dt_mode": ["stable", "naive", "fp64"][args.dt_mode],
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+        "ms_per_cg_iter": total_ms / args.steps / n_iter,
+        "ms_per_J": 1e3 * j_avg, "ms_per_JT": 1e3 * jt_avg,
+        "J_evals_per_s": support / j_avg, "JT_evals_per_s": support / jt_avg,
+        "setup_ms": {"table": 1e3 * (t1 - t0), "geometry_and_cull": 1e3 * (t2 - t1)},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
+                     "frac": achieved / peak_evals, "traffic": APPLY_TRAFFIC_BYTES,
+                     "kernel": "apply_kernel (J^T) + jt_reduce",
+                     "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM_CLK} FP32 lanes x {sm_max:.0f} MHz "
+                                   f"({pk_kind}) / {OPS_PER_EVAL} ops per eval"},
+        "err_vs_fp64_oracle": err,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * evals_per_step / (e2e_total * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * geo.M, "d2h_bytes_per_step": 4 * geo.V,
+                "ms_per_step": e2e_total},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * fft_gb300.h - C ABI of the GB300 (sm_103a) finite-frequency traveltime tomography library.
+ *
+ * The library applies the linearised cross-correlation traveltime operator of
+ * Korta Martiartu, Boehm and Fichtner, "3D wave-equation-based finite-frequency tomography
+ * for ultrasound computed tomography" (arXiv:1908.03302):
+ *
+ *   dT_p = sum_v J[p, v] dc_v,   J[p, v] = K0(x_v; x_s(p), x_r(p)) * h^3           (Eq. forward_compact)
+ *   K0(x) = A(x) * Phi(dt),      A = -R_sr / (2 pi c0^3 R_xs R_xr)                 (Eq. Linearized_sensitivity)
+ *   Phi(dt) = int w^3 W(w) sin(w dt) dw / int w^2 W(w) dw, W = |f(w)|^2             (Eq. Kernel_freq)
+ *   dt = (R_xs + R_xr - R_sr) / c0, Phi = 0 for dt >= dt_max (truncation)          (Sec. II-C)
+ *
+ * and its adjoint, without ever storing J (entries are rebuilt on the fly in every call,
+ * Sec. II-C), a damped least-squares CG solve (Sec. II-D, Eq. leastSquare_misfit) and
+ * Hessian point-spread functions H e_k = J^T J e_k (Sec. II-D, Eq. resolution_2).
+ *
+ * Conventions shared by every call
+ *   - Units are SI at the boundary: metres, seconds, m/s.
+ *   - Rows (measurements) are emitter/receiver pairs in the caller's order; a row may carry a
+ *     frequency band (its own Phi table). Voxels are the centres of a regular grid,
+ *     v = (k * ny + j) * nx + i, x fastest; voxel (i, j, k) sits at origin + (i, j, k) * h.
+ *   - Vectors m (length V = nx*ny*nz, m/s) and d (length M, s) are float32 device arrays
+ *     owned by the caller. Handles own everything else (tables, pair records, cull lists,
+ *     scratch), allocated at creation on the current device.
+ *   - All apply/solve calls are asynchronous on the caller's CUDA stream (cudaStream_t passed
+ *     as void*, NULL = legacy default stream) unless stated otherwise. A handle may be used
+ *     by one stream at a time: its scratch buffers are shared by its calls.
+ *   - Every call returns an fft_status; on failure fft_last_error() gives a message
+ *     (thread-local). No C++ exception crosses this boundary.
+ */
+#ifndef FFT_GB300_H
+#define FFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fft_status;
+#define FFT_OK 0
+#define FFT_ERR_ARG (-1)       /* invalid argument (null pointer, bad size, bad mode) */
+#define FFT_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define FFT_ERR_OOM (-3)       /* device allocation failed */
+#define FFT_ERR_BREAKDOWN (-4) /* CG breakdown: a curvature <= 0 or a non-finite scalar */
+#define FFT_ERR_TIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define FFT_ERR_STATE (-6)     /* handle in the wrong state (e.g. used on another device) */
+
+/* Detour-time arithmetic inside the J / J^T kernels (chosen per geometry). */
+#define FFT_DT_STABLE 0 /* FP32, cancellation-free form in the pair frame (default) */
+#define FFT_DT_NAIVE 1  /* FP32, R_xs + R_xr - L by plain subtraction */
+#define FFT_DT_FP64 2   /* detour in FP64, rest in FP32 (slow; precision studies) */
+
+/* Source power spectrum W(w) = |f(w)|^2 (Eq. Kernel_freq).
+ *   kind 0: Gaussian in frequency, W = exp(-(w-w0)^2/(2 s^2)) + exp(-(w+w0)^2/(2 s^2)),
+ *           w0 = 2 pi f_center_hz, s = 2 pi f_sigma_hz (even extension to w < 0).
+ *   kind 1: sampled, W(omega[j]) = weight[j] at ascending angular frequencies (host arrays,
+ *           n_omega >= 2, read during the call only). */
+typedef struct {
+    int32_t kind;
+    double f_center_hz;
+    double f_sigma_hz;
+    const double* omega;
+    const double* weight;
+    int32_t n_omega;
+} fft_spectrum;
+
+/* Voxel grid: nx, ny, nz >= 1; h > 0 the spacing; origin the centre of voxel (0, 0, 0). */
+typedef struct {
+    int32_t nx, ny, nz;
+    double h;
+    double origin[3];
+} fft_grid;
+
+typedef struct fft_table_s* fft_table; /* opaque: one sampled Phi table */
+typedef struct fft_geom_s* fft_geom;   /* opaque: rows + grid + tables + cull lists */
+
+/*
+ * fft_table_build - sample Phi(dt_k), dt_k = k dt_max / (n_samples - 1), k = 0..n-1,
+ * by FP64 quadrature on the device (Eq. Kernel_freq with upper limits read as infinity;
+ * the sampled table is what Sec. II-C stores in place of F).
+ *   spec       spectrum (host struct; sampled arrays are host memory).
+ *   n_samples  2 .. 65536 (4096 in the reference workloads).
+ *   dt_max     cut-off detour time in s (> 0); Phi is 0 at and beyond it.
+ *   host_out   nullable; if given, receives the n_samples FP64 values (the call then
+ *              synchronises with the device).
+ *   out        receives the new handle; release with fft_table_destroy.
+ * Quadrature: kind 0 composite Simpson over [0, w0 + 12 s] with 40000 intervals; kind 1
+ * trapezoid rule over the given nodes. Synchronous apart from the optional copy above.
+ */
+fft_status fft_table_build(const fft_spectrum* spec, int32_t n_samples, double dt_max,
+                           double* host_out, fft_table* out);
+void fft_table_destroy(fft_table t);
+
+/*
+ * fft_geom_create - set up the operator J for one acquisition (Eq. forward_compact):
+ *   tx_xyz       host, n_tx x 3 transducer positions (m).
+ *   rows         host, n_rows x 2 (s, r) transducer indices, s != r. Row order is the
+ *                order of d.
+ *   band_of_row  host, nullable (all rows use table 0), else n_rows table indices.
+ *   grid         voxel grid (host struct).
+ *   c0           background sound speed (m/s) > 0.
+ *   tables       host array of n_tables handles (1..8).
+ *   dt_mode      FFT_DT_STABLE / FFT_DT_NAIVE / FFT_DT_FP64.
+ * Builds per-row records and the culled (tile, row) lists on the device: a (16x16x8 voxel
+ * tile, row) entry is kept unless a lower bound of the detour over the tile (tangent plane
+ * of the convex R at the tile centre) proves dt >= dt_max everywhere in it. Synchronous.
+ * Fails with FFT_ERR_ARG for empty inputs, out-of-range indices or s == r.
+ */
+fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const int32_t* rows,
+                           int64_t n_rows, const int32_t* band_of_row, const fft_grid* grid,
+                           double c0, const fft_table* tables, int32_t n_tables,
+                           int32_t dt_mode, fft_geom* out);
+void fft_geom_destroy(fft_geom g);
+
+/* Sizes and counters of a geometry (host struct filled synchronously). */
+typedef struct {
+    int64_t n_rows;          /* M */
+    int64_t n_vox;           /* V */
+    int64_t n_entries;       /* kept (tile, row) entries */
+    int64_t n_items;         /* work items of one apply */
+    int64_t support_evals;   /* (row, voxel) pairs with 0 <= dt < dt_max: in-support evaluations
+                                of one J or J^T (counted on the device at creation) */
+    int64_t scratch_bytes;   /* device bytes owned by the handle */
+    int32_t dt_mode;
+} fft_geom_info_t;
+fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info);
+
+/*
+ * fft_J_apply - d = J m (Eq. forward_compact; m in m/s, d in s).
+ *   m_dev  device float32[V]; d_dev device float32[M] (written entirely). No aliasing.
+ * Each row's value is a fixed-order sum (deterministic, bit-reproducible run to run).
+ */
+fft_status fft_J_apply(fft_geom g, const float* m_dev, float* d_dev, void* stream);
+
+/*
+ * fft_JT_apply - g = J^T d (the adjoint used by the normal equations, Eq. leastSquare_misfit).
+ *   d_dev device float32[M]; g_dev device float32[V] (written entirely). Gather per voxel,
+ *   no atomics; deterministic.
+ */
+fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev, void* stream);
+
+/*
+ * fft_frob2 - |J|_F^2 = sum over rows and voxels of J[p, v]^2, computed on the device with
+ * FP64 accumulation; synchronous; cached in the handle after the first call.
+ */
+fft_status fft_frob2(fft_geom g, double* out);
+
+/*
+ * fft_cg_solve - damped least squares (Sec. II-D, Eq. leastSquare_misfit with
+ * Gamma_n = I, Gamma_pr = I): minimise 1/2 |J m - d|^2 + 1/2 lambda |m|^2 by CGLS,
+ * n_iter iterations, no early stop. lambda = lambda_rel * |J|_F^2 / V (the mean diagonal of
+ * J^T J), so lambda_rel is dimensionless.
+ *   d_dev     device float32[M] data.
+ *   m_dev     device float32[V]: in = starting model (zeros for m0 = 0), out = solution.
+ *   hist_host nullable host double[n_iter + 1]: |J^T r - lambda m|^2 before each iteration
+ *             and after the last (the call then synchronises).
+ * Vectors are FP32; inner products, alpha, beta and gamma are FP64 on the device (no host
+ * round trip). The iteration loop is captured once per handle into a CUDA graph and
+ * replayed. Returns FFT_ERR_BREAKDOWN (after synchronising) if a curvature was <= 0 or a
+ * scalar became non-finite; the iterations after a breakdown leave m unchanged.
+ */
+fft_status fft_cg_solve(fft_geom g, const float* d_dev, double lambda_rel, int32_t n_iter,
+                        float* m_dev, double* hist_host, void* stream);
+
+/*
+ * fft_psf_batch - Hessian point-spread functions (Sec. II-D, Eq. resolution_2):
+ *   out[(s * n_spike + k) * V + v] = sum_{p in S_s} J[p, v] J[p, spike_vox[k]]
+ * i.e. H_S e_k with a unit (1 m/s) spike, for every row subset S_s and spike k.
+ *   spike_vox     host int64[n_spike] voxel indices (0 <= . < V).
+ *   subset_off    host int32[n_subsets + 1] CSR offsets into subset_rows.
+ *   subset_rows   host int32[subset_off[n_subsets]] row indices (each subset ascending).
+ *   mode          0: FP32 CUDA-core path.
+ *   out_dev       device float32[n_subsets * n_spike * V], written entirely.
+ */
+fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
+                         const int32_t* subset_off, int32_t n_subsets,
+                         const int32_t* subset_rows, int32_t mode, float* out_dev, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* fft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFT_GB300_H */

@@ -1,0 +1,267 @@
+"""GB300-native finite-frequency traveltime tomography (arXiv:1908.03302).
+
+Python face of the CUDA library ``libfft_gb300.so`` (C ABI in ``include/fft_gb300.h``).
+PyTorch supplies device memory and the current stream; the computation itself runs in the
+library's kernels. The functions mirror the C entry points:
+
+* ``fft_table_build``  - sample the Phi function of a source spectrum (Eq. Kernel_freq)
+* ``fft_geom_create``  - rows, voxel grid and tables -> an operator handle (Eq. forward_compact)
+* ``fft_J_apply`` / ``fft_JT_apply`` - d = J m and g = J^T d, entries rebuilt on the fly
+* ``fft_cg_solve``     - damped least squares by CGLS (Eq. leastSquare_misfit)
+* ``fft_psf_batch``    - Hessian point-spread functions J_S^T J_S e_k (Eq. resolution_2)
+
+``Table`` and ``Geometry`` wrap the handles; ``JFunction`` / ``jacobian_apply`` put J behind
+``torch.autograd`` with J^T as its backward.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import (FFT_DT_FP64, FFT_DT_NAIVE, FFT_DT_STABLE, FFTError, check, fft_geom_info_t,
+                   fft_grid, fft_spectrum)
+
+__all__ = [
+    "Table", "Geometry", "JFunction", "jacobian_apply", "FFTError",
+    "fft_table_build", "fft_geom_create", "fft_J_apply", "fft_JT_apply", "fft_cg_solve", "fft_psf_batch",
+    "FFT_DT_STABLE", "FFT_DT_NAIVE", "FFT_DT_FP64", "fresnel_width", "build",
+]
+
+
+def build(force: bool = False) -> str:
+    """Compile libfft_gb300.so for sm_103a (no-op when up to date)."""
+    from . import _buildlib
+    return _buildlib.build(force=force)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _dev_ptr(t, n: Optional[int] = None, name: str = "tensor") -> int:
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return int(t.data_ptr())
+
+
+def fresnel_width(c0: float, length: float, f_center: float) -> float:
+    """Width sqrt(c0 L / f) of the first Fresnel zone of a pair of length L (Sec. IV)."""
+    return float(np.sqrt(c0 * length / f_center))
+
+
+# --------------------------------------------------------------------------- tables
+
+class Table:
+    """Sampled Phi(dt_k), dt_k = k dt_max / (n - 1), built on the device in FP64."""
+
+    def __init__(self, f_center: Optional[float] = None, f_sigma: Optional[float] = None, n: int = 4096,
+                 dt_max: Optional[float] = None, omega: Optional[np.ndarray] = None,
+                 weight: Optional[np.ndarray] = None, keep_host: bool = False):
+        L = _lib.load()
+        spec = fft_spectrum()
+        self._keep = []
+        if omega is None:
+            spec.kind, spec.f_center_hz, spec.f_sigma_hz = 0, float(f_center), float(f_sigma)
+            spec.omega = spec.weight = None
+            spec.n_omega = 0
+        else:
+            om = np.ascontiguousarray(omega, dtype=np.float64)
+            w = np.ascontiguousarray(weight, dtype=np.float64)
+            self._keep = [om, w]
+            spec.kind, spec.f_center_hz, spec.f_sigma_hz = 1, 0.0, 0.0
+            spec.omega, spec.weight, spec.n_omega = om.ctypes.data, w.ctypes.data, len(om)
+        if dt_max is None:
+            dt_max = 3.0 / float(f_center)
+        self.n = int(n)
+        self.dt_max = float(dt_max)
+        host = np.empty(self.n) if keep_host else None
+        h = ctypes.c_void_p()
+        check(L.fft_table_build(ctypes.byref(spec), self.n, self.dt_max,
+                                None if host is None else host.ctypes.data, ctypes.byref(h)))
+        self.handle = h
+        self.host = host
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib.load().fft_table_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fft_table_build(f_center=None, f_sigma=None, n=4096, dt_max=None, omega=None, weight=None,
+                    keep_host=False) -> Table:
+    return Table(f_center, f_sigma, n, dt_max, omega, weight, keep_host)
+
+
+# --------------------------------------------------------------------------- geometry
+
+class Geometry:
+    """Operator handle: rows (emitter, receiver, band), voxel grid, c0 and Phi tables."""
+
+    def __init__(self, tx: np.ndarray, rows: np.ndarray, grid, c0: float, tables: Sequence[Table],
+                 band_of_row: Optional[np.ndarray] = None, dt_mode: int = FFT_DT_STABLE):
+        L = _lib.load()
+        self._tx = np.ascontiguousarray(tx, dtype=np.float64).reshape(-1, 3)
+        self._rows = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1, 2)
+        self._band = None if band_of_row is None else np.ascontiguousarray(band_of_row, dtype=np.int32)
+        g = fft_grid()
+        g.nx, g.ny, g.nz, g.h = int(grid.nx), int(grid.ny), int(grid.nz), float(grid.h)
+        for a in range(3):
+            g.origin[a] = float(grid.origin[a])
+        self.grid = grid
+        self.tables = list(tables)
+        arr = (ctypes.c_void_p * len(self.tables))(*[t.handle.value for t in self.tables])
+        h = ctypes.c_void_p()
+        check(L.fft_geom_create(self._tx.ctypes.data, len(self._tx), self._rows.ctypes.data, len(self._rows),
+                                None if self._band is None else self._band.ctypes.data, ctypes.byref(g),
+                                float(c0), ctypes.cast(arr, ctypes.c_void_p), len(self.tables), int(dt_mode),
+                                ctypes.byref(h)))
+        self.handle = h
+        self.c0 = float(c0)
+        info = self.info()
+        self.M = int(info.n_rows)
+        self.V = int(info.n_vox)
+
+    def info(self) -> fft_geom_info_t:
+        out = fft_geom_info_t()
+        check(_lib.load().fft_geom_info(self.handle, ctypes.byref(out)))
+        return out
+
+    @property
+    def support_evals(self) -> int:
+        return int(self.info().support_evals)
+
+    def J(self, m, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.M, device=m.device, dtype=torch.float32)
+        check(_lib.load().fft_J_apply(self.handle, _dev_ptr(m, self.V, "m"), _dev_ptr(out, self.M, "d"),
+                                      _stream_handle(stream)))
+        return out
+
+    def JT(self, d, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.V, device=d.device, dtype=torch.float32)
+        check(_lib.load().fft_JT_apply(self.handle, _dev_ptr(d, self.M, "d"), _dev_ptr(out, self.V, "g"),
+                                       _stream_handle(stream)))
+        return out
+
+    def frob2(self) -> float:
+        v = ctypes.c_double()
+        check(_lib.load().fft_frob2(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def cg_solve(self, d, lambda_rel: float, n_iter: int, m=None, with_history: bool = False, stream=None):
+        torch = _torch()
+        if m is None:
+            m = torch.zeros(self.V, device=d.device, dtype=torch.float32)
+        hist = np.empty(n_iter + 1) if with_history else None
+        check(_lib.load().fft_cg_solve(self.handle, _dev_ptr(d, self.M, "d"), float(lambda_rel), int(n_iter),
+                                       _dev_ptr(m, self.V, "m"), None if hist is None else hist.ctypes.data,
+                                       _stream_handle(stream)))
+        return (m, hist) if with_history else m
+
+    def psf_batch(self, spikes: Sequence[int], subsets: Sequence[np.ndarray], mode: int = 0, out=None, stream=None):
+        torch = _torch()
+        sp = np.ascontiguousarray(spikes, dtype=np.int64)
+        off = np.zeros(len(subsets) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([len(s) for s in subsets])
+        idx = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.int32) for s in subsets])
+                                   if len(subsets) else np.zeros(0, np.int32), dtype=np.int32)
+        n = len(subsets) * len(sp) * self.V
+        if out is None:
+            out = torch.empty(n, device="cuda", dtype=torch.float32)
+        check(_lib.load().fft_psf_batch(self.handle, sp.ctypes.data, len(sp), off.ctypes.data, len(subsets),
+                                        idx.ctypes.data if len(idx) else None, int(mode), _dev_ptr(out, n, "out"),
+                                        _stream_handle(stream)))
+        return out.view(len(subsets), len(sp), self.V)
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib.load().fft_geom_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fft_geom_create(tx, rows, grid, c0, tables, band_of_row=None, dt_mode=FFT_DT_STABLE) -> Geometry:
+    return Geometry(tx, rows, grid, c0, tables, band_of_row, dt_mode)
+
+
+def fft_J_apply(geom: Geometry, m, d=None, stream=None):
+    return geom.J(m, d, stream)
+
+
+def fft_JT_apply(geom: Geometry, d, g=None, stream=None):
+    return geom.JT(d, g, stream)
+
+
+def fft_cg_solve(geom: Geometry, d, lambda_rel: float, n_iter: int, m=None, with_history=False, stream=None):
+    return geom.cg_solve(d, lambda_rel, n_iter, m, with_history, stream)
+
+
+def fft_psf_batch(geom: Geometry, spikes, subsets, mode=0, out=None, stream=None):
+    return geom.psf_batch(spikes, subsets, mode, out, stream)
+
+
+# --------------------------------------------------------------------------- autograd
+
+def _make_jfunction():
+    torch = _torch()
+
+    class JFunction(torch.autograd.Function):
+        """d = J m with the hand-written adjoint as backward: grad_m = J^T grad_d."""
+
+        @staticmethod
+        def forward(ctx, m, geom):
+            ctx.geom = geom
+            return geom.J(m.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad_d):
+            return ctx.geom.JT(grad_d.contiguous()), None
+
+    return JFunction
+
+
+_JF = None
+
+
+def __getattr__(name):
+    global _JF
+    if name == "JFunction":
+        if _JF is None:
+            _JF = _make_jfunction()
+        return _JF
+    raise AttributeError(name)
+
+
+def jacobian_apply(m, geom: Geometry):
+    """Differentiable d = J m (backward runs the J^T kernel)."""
+    global _JF
+    if _JF is None:
+        _JF = _make_jfunction()
+    return _JF.apply(m, geom)

@@ -1,0 +1,506 @@
+// J m and J^T d, rebuilt on the fly (Sec. II-C: "the elements of F are computed on the fly
+// through the matrix-vector products"), tile-centric on sm_103a.
+//
+// Work decomposition
+//   * The voxel grid is cut into 16 x 16 x 8 tiles. Each tile has a list of candidate rows
+//     (built once per geometry by a conservative cull). A work item is a tile and a range of
+//     its rows; persistent CTAs pull items from a counter, heaviest first.
+//   * In a CTA, warp w owns a fixed 8 x 8 x 4 region of the tile (two 8 x 4 x 4 sub-bricks);
+//     lane l owns 4 consecutive x voxels of each sub-brick. All warps stream the item's rows
+//     independently: per chunk of 32 rows, lane l loads row l, moves its geometry into the
+//     tile's pair frame and tests it against the warp's two sub-bricks (tangent-plane bound
+//     of the convex detour); the survivors are staged in shared memory and broadcast.
+//   * Per (row, voxel): pair-frame coordinates by FFMA from per-lane offsets, normalised
+//     detour (cancellation-free form), Phi from the band table in shared memory (one 64-bit
+//     load, linear interpolation), geometric factor 1 / (R_xs R_xr).
+//   * J^T accumulates per voxel in registers over the item's rows (gather, no atomics).
+//     J reduces per row over the warp (shuffles) and writes one partial per (entry, warp);
+//     a second kernel sums each row's partials in a fixed order. Both are deterministic.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <vector>
+
+#include "fft_common.cuh"
+#include "fft_device.cuh"
+
+namespace fftgb {
+
+enum { MODE_JT = 0, MODE_J = 1, MODE_COUNT = 2, MODE_FROB = 3 };
+
+struct ApplyParams {
+    const RowRec* rec;
+    const RowRec64* rec64;
+    const int32_t* row_band;
+    const float2* tab;
+    int n_bands;
+    int n_tab;
+    const BandConst* bc;     // device [n_bands]
+    const int32_t* tile_rows;
+    const Item* items;
+    int n_items;
+    int32_t* counter;
+    int tiles_x, tiles_y;
+    int nx, ny, nz;
+    double org[3];
+    double h;
+    const float* vin;        // J: m [V]; J^T: d [M]
+    float* vout;             // J: jpart [E * 8]; J^T: g [V]
+    float* gpart;            // J^T partials of multi-item tiles
+    double* dsum;            // FROB: [n_items * 8]
+    unsigned long long* icount;   // COUNT
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP64 detour for the precision-study mode: voxel (ix, iy, iz), row record in metres.
+__device__ __forceinline__ float detour_v64(const RowRec64& r, double ox, double oy, double oz, double h,
+                                            int ix, int iy, int iz, double U, float& w_band) {
+    double x = ox + ix * h, y = oy + iy * h, z = oz + iz * h;
+    double ex = r.xr[0] - r.xs[0], ey = r.xr[1] - r.xs[1], ez = r.xr[2] - r.xs[2];
+    double L = sqrt(ex * ex + ey * ey + ez * ez);
+    ex /= L; ey /= L; ez /= L;
+    double dx = x - 0.5 * (r.xs[0] + r.xr[0]), dy = y - 0.5 * (r.xs[1] + r.xr[1]),
+           dz = z - 0.5 * (r.xs[2] + r.xr[2]);
+    double p = dx * ex + dy * ey + dz * ez;
+    double c1 = dy * ez - dz * ey, c2 = dz * ex - dx * ez, c3 = dx * ey - dy * ex;
+    double q2 = c1 * c1 + c2 * c2 + c3 * c3;
+    double hl = 0.5 * L, ps = p + hl, pr = p - hl;
+    double Rs = sqrt(ps * ps + q2), Rr = sqrt(pr * pr + q2);
+    if (Rs == 0.0 || Rr == 0.0) {
+        w_band = 0.0f;
+        return 0.0f;
+    }
+    double A = Rs + fabs(ps), B = Rr + fabs(pr);
+    double R = q2 * (A + B) / (A * B) + ((fabs(ps) - ps) + (fabs(pr) + pr));
+    w_band = (float)(U * U / (Rs * Rr));
+    double v = R / U;
+    return (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
+}
+
+template <int MODE, int DT, bool GUARD>
+__global__ void __launch_bounds__(APPLY_THREADS, 2) apply_kernel(const __grid_constant__ ApplyParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* s_tab = reinterpret_cast<float2*>(smem);
+    const int tab_len = P.n_bands * P.n_tab;
+    float4* s_stage = reinterpret_cast<float4*>(smem + (((size_t)tab_len * sizeof(float2) + 15) & ~(size_t)15));
+    __shared__ int s_item;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < tab_len; i += APPLY_THREADS) s_tab[i] = P.tab[i];
+
+    const uint32_t tab_addr = smem_addr(s_tab);
+    const float nm1 = (float)(P.n_tab - 1);
+    const int wx = warp & 1, wy = (warp >> 1) & 1, wz = warp >> 2;
+    const int lx = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
+    // lane voxel offsets in the tile (sub-brick 0, first of its 4 x voxels)
+    const int oxi = 8 * wx + 4 * lx, oyi = 8 * wy + ly, ozi = 4 * wz + lz;
+    const float Xl = (float)oxi, Yl = (float)oyi, Zl = (float)ozi;
+    float4* stg = s_stage + warp * 96;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(P.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= P.n_items) break;
+        const Item item = P.items[it];
+        const int tx = item.tile % P.tiles_x;
+        const int ty = (item.tile / P.tiles_x) % P.tiles_y;
+        const int tz = item.tile / (P.tiles_x * P.tiles_y);
+        const int TX = TILE_X * tx, TY = TILE_Y * ty, TZ = TILE_Z * tz;
+
+        // validity of this lane's voxels and of the warp's sub-bricks
+        const bool zin = (TZ + ozi) < P.nz;
+        bool vin_[2][NX_LANE];
+        int64_t vidx[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int y = TY + oyi + 4 * s;
+            vidx[s] = ((int64_t)(TZ + ozi) * P.ny + y) * P.nx + TX + oxi;
+#pragma unroll
+            for (int t = 0; t < NX_LANE; ++t) vin_[s][t] = zin && (y < P.ny) && (TX + oxi + t < P.nx);
+        }
+        const bool sub_ok0 = (TX + 8 * wx < P.nx) && (TY + 8 * wy < P.ny) && (TZ + 4 * wz < P.nz);
+        const bool sub_ok1 = (TX + 8 * wx < P.nx) && (TY + 8 * wy + 4 < P.ny) && (TZ + 4 * wz < P.nz);
+
+        float acc[2][NX_LANE];
+        float mv[2][NX_LANE];
+        double dacc = 0.0;
+        unsigned long long cnt = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int t = 0; t < NX_LANE; ++t) {
+                acc[s][t] = 0.0f;
+                mv[s][t] = 0.0f;
+                if (MODE == MODE_J && vin_[s][t]) mv[s][t] = __ldg(P.vin + vidx[s] + t);
+            }
+
+        for (int64_t e0 = item.e0; e0 < item.e1; e0 += 32) {
+            // ---- stage: lane l prepares row e0 + l
+            const int64_t e = e0 + lane;
+            const bool have = e < item.e1;
+            bool ok0 = false, ok1 = false;
+            if (have) {
+                const int p = P.tile_rows[e];
+                const RowRec r = P.rec[p];
+                const int b = P.row_band[p];
+                const BandConst bc = P.bc[b];
+                const float hb = bc.h;
+                float W = r.b.w;
+                if (MODE == MODE_JT) W *= __ldg(P.vin + p);
+                const float dx = fmaf((float)TX, hb, bc.org[0]) - r.a.x;
+                const float dy = fmaf((float)TY, hb, bc.org[1]) - r.a.y;
+                const float dz = fmaf((float)TZ, hb, bc.org[2]) - r.a.z;
+                const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
+                const float pT = fmaf(dx, ex, fmaf(dy, ey, dz * ez));
+                const float c1T = fmaf(dy, ez, -dz * ey);
+                const float c2T = fmaf(dz, ex, -dx * ez);
+                const float c3T = fmaf(dx, ey, -dy * ex);
+                const float hx = hb * ex, hy = hb * ey, hz = hb * ez;
+                // sub-brick centres relative to the pair midpoint
+                const float cx = fmaf(8.0f * wx + 3.5f, hb, dx);
+                const float cz = fmaf(4.0f * wz + 1.5f, hb, dz);
+                const float cy0 = fmaf(8.0f * wy + 1.5f, hb, dy);
+                const float cy1 = fmaf(8.0f * wy + 5.5f, hb, dy);
+                const float hxx = 3.5f * hb, hyy = 1.5f * hb;
+                // rows with zero weight add exactly nothing to J^T: skip them
+                const bool live = (MODE != MODE_JT) || (W != 0.0f);
+                ok0 = live && sub_ok0 && box_may_touch(cx, cy0, cz, ex, ey, ez, hl, hxx, hyy, hyy);
+                ok1 = live && sub_ok1 && box_may_touch(cx, cy1, cz, ex, ey, ez, hl, hxx, hyy, hyy);
+                const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
+                stg[lane * 3 + 0] = make_float4(pT, c1T, c2T, c3T);
+                stg[lane * 3 + 1] = make_float4(hx, hy, hz, hl);
+                stg[lane * 3 + 2] = make_float4(W, __uint_as_float(tb), __int_as_float(p), __int_as_float(b));
+            }
+            const uint32_t m0 = __ballot_sync(0xffffffffu, ok0);
+            const uint32_t m1 = __ballot_sync(0xffffffffu, ok1);
+            __syncwarp();
+            uint32_t mm = m0 | m1;
+            float mypart = 0.0f;
+            while (mm) {
+                const int bit = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const float4 A = stg[bit * 3 + 0];
+                const float4 B = stg[bit * 3 + 1];
+                const float4 C = stg[bit * 3 + 2];
+                const float hx = B.x, hy = B.y, hz = B.z, hl = B.w, W = C.x;
+                const uint32_t tb = __float_as_uint(C.y);
+                // lane base (sub-brick 0, t = 0) in the pair frame
+                float pb = fmaf(Xl, hx, fmaf(Yl, hy, fmaf(Zl, hz, A.x)));
+                float c1 = fmaf(Yl, hz, fmaf(-Zl, hy, A.y));
+                float c2 = fmaf(Zl, hx, fmaf(-Xl, hz, A.z));
+                float c3 = fmaf(Xl, hy, fmaf(-Yl, hx, A.w));
+                float part = 0.0f;
+#pragma unroll
+                for (int s = 0; s < 2; ++s) {
+                    const uint32_t ms = s ? m1 : m0;
+                    if (s == 1) {
+                        pb = fmaf(4.0f, hy, pb);
+                        c1 = fmaf(4.0f, hz, c1);
+                        c3 = fmaf(-4.0f, hx, c3);
+                    }
+                    if (!((ms >> bit) & 1u)) continue;
+                    const float c1sq = c1 * c1;
+#pragma unroll
+                    for (int t = 0; t < NX_LANE; ++t) {
+                        const float ft = (float)t;
+                        float is, ir, v, w;
+                        if (DT == FFT_DT_FP64) {
+                            const RowRec64 r64 = P.rec64[__float_as_int(C.z)];
+                            const int b = __float_as_int(C.w);
+                            v = detour_v64(r64, P.org[0], P.org[1], P.org[2], P.h, TX + oxi + t,
+                                           TY + oyi + 4 * s, TZ + ozi, P.bc[b].U, w);
+                            is = 1.0f;
+                            ir = w;
+                        } else {
+                            const float pt = fmaf(ft, hx, pb);
+                            const float c2t = fmaf(-ft, hz, c2);
+                            const float c3t = fmaf(ft, hy, c3);
+                            const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
+                            v = detour_v<DT, GUARD>(pt, q2, hl, is, ir);
+                        }
+                        if (MODE == MODE_COUNT) {
+                            if (vin_[s][t] && v < 1.0f) ++cnt;
+                            continue;
+                        }
+                        const float val = phi_lookup(v, tb, nm1) * (is * ir);
+                        if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);
+                        if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);
+                        if (MODE == MODE_FROB) {
+                            if (vin_[s][t]) part = fmaf(val, val, part);
+                        }
+                    }
+                }
+                if (MODE == MODE_J) {
+                    part = warp_sum(part);
+                    if (lane == bit) mypart = part * W;
+                }
+                if (MODE == MODE_FROB) dacc += (double)part * (double)W * (double)W;
+            }
+            if (MODE == MODE_J && have) P.vout[e * 8 + warp] = mypart;
+            __syncwarp();
+        }
+
+        if (MODE == MODE_JT) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                if (item.slot < 0) {
+#pragma unroll
+                    for (int t = 0; t < NX_LANE; ++t)
+                        if (vin_[s][t]) P.vout[vidx[s] + t] = acc[s][t];
+                } else {
+                    // local index inside the tile: (z * 16 + y) * 16 + x
+                    const int loc = ((ozi * TILE_Y) + oyi + 4 * s) * TILE_X + oxi;
+                    float4 v4 = make_float4(acc[s][0], acc[s][1], acc[s][2], acc[s][3]);
+                    *reinterpret_cast<float4*>(P.gpart + (int64_t)item.slot * TILE_VOX + loc) = v4;
+                }
+            }
+        }
+        if (MODE == MODE_FROB) {
+            dacc = warp_sum_d(dacc);
+            if (lane == 0) P.dsum[(int64_t)it * APPLY_WARPS + warp] = dacc;
+        }
+        if (MODE == MODE_COUNT) {
+            unsigned long long c = cnt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            if (lane == 0 && c) atomicAdd(P.icount, c);
+        }
+    }
+}
+
+// d_p = sum over the row's entries (ascending tile order) and the 8 warps of the partials.
+__global__ void j_reduce_kernel(const int64_t* __restrict__ row_off, const int64_t* __restrict__ row_ent,
+                                const float* __restrict__ jpart, int64_t M, float* __restrict__ d) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    double s = 0.0;
+    for (int64_t j = row_off[p]; j < row_off[p + 1]; ++j) {
+        const float4* q = reinterpret_cast<const float4*>(jpart + row_ent[j] * 8);
+        float4 a = q[0], b = q[1];
+        s += (double)a.x + (double)a.y + (double)a.z + (double)a.w + (double)b.x + (double)b.y +
+             (double)b.z + (double)b.w;
+    }
+    d[p] = (float)s;
+}
+
+// g for voxels of tiles with several items (sum of slots in item order) or with none (0).
+__global__ void jt_reduce_kernel(const int32_t* __restrict__ slot0, const int32_t* __restrict__ nslot,
+                                 const float* __restrict__ gpart, int nx, int ny, int nz, int tiles_x,
+                                 int tiles_y, float* __restrict__ g) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t V = (int64_t)nx * ny * nz;
+    if (v >= V) return;
+    int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
+    int T = (k / TILE_Z * tiles_y + j / TILE_Y) * tiles_x + i / TILE_X;
+    int s0 = slot0[T];
+    if (s0 == -1) return;
+    if (s0 == -2) {
+        g[v] = 0.0f;
+        return;
+    }
+    int loc = ((k % TILE_Z) * TILE_Y + (j % TILE_Y)) * TILE_X + (i % TILE_X);
+    float s = 0.0f;
+    for (int q = 0; q < nslot[T]; ++q) s += gpart[(int64_t)(s0 + q) * TILE_VOX + loc];
+    g[v] = s;
+}
+
+static ApplyParams make_params(fft_geom g) {
+    ApplyParams P;
+    P.rec = g->rec;
+    P.rec64 = g->rec64;
+    P.row_band = g->row_band;
+    P.tab = g->tab;
+    P.n_bands = g->n_bands;
+    P.n_tab = g->n_tab;
+    P.bc = g->d_band;
+    P.tile_rows = g->tile_rows;
+    P.items = g->items;
+    P.n_items = g->n_items;
+    P.counter = g->counter;
+    P.tiles_x = g->tiles[0];
+    P.tiles_y = g->tiles[1];
+    P.nx = g->grid.nx;
+    P.ny = g->grid.ny;
+    P.nz = g->grid.nz;
+    for (int a = 0; a < 3; ++a) P.org[a] = g->grid.origin[a];
+    P.h = g->grid.h;
+    P.vin = nullptr;
+    P.vout = nullptr;
+    P.gpart = g->gpart;
+    P.dsum = nullptr;
+    P.icount = nullptr;
+    return P;
+}
+
+size_t apply_smem(fft_geom g) {
+    size_t tab = ((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15;
+    return tab + (size_t)APPLY_WARPS * 96 * sizeof(float4);
+}
+
+template <int MODE, int DT, bool G>
+static fft_status set_attr_one(size_t smem) {
+    FFT_CUDA(cudaFuncSetAttribute(apply_kernel<MODE, DT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    return FFT_OK;
+}
+
+template <int MODE>
+static fft_status set_attr_mode(size_t smem) {
+    fft_status rc;
+    if ((rc = set_attr_one<MODE, FFT_DT_STABLE, false>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_one<MODE, FFT_DT_STABLE, true>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_one<MODE, FFT_DT_NAIVE, false>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_one<MODE, FFT_DT_NAIVE, true>(smem)) != FFT_OK) return rc;
+    return set_attr_one<MODE, FFT_DT_FP64, false>(smem);
+}
+
+// Raise the dynamic shared-memory limit of every kernel instantiation once per geometry
+// (outside any stream capture), so launches need no attribute calls.
+fft_status set_apply_attributes(fft_geom g) {
+    const size_t smem = apply_smem(g);
+    fft_status rc;
+    if ((rc = set_attr_mode<MODE_JT>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_mode<MODE_J>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_mode<MODE_COUNT>(smem)) != FFT_OK) return rc;
+    return set_attr_mode<MODE_FROB>(smem);
+}
+
+// Persistent grid size: resident CTAs per SM of the J^T kernel times the SM count.
+int apply_occupancy(fft_geom g) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<MODE_JT, FFT_DT_STABLE, false>,
+                                                  APPLY_THREADS, apply_smem(g));
+    if (per_sm < 1) per_sm = 1;
+    if (sms < 1) sms = 1;
+    return per_sm * sms;
+}
+
+template <int MODE>
+static fft_status launch_mode(fft_geom g, const ApplyParams& P, cudaStream_t st) {
+    const size_t smem = apply_smem(g);
+    const int ctas = g->apply_ctas;
+    FFT_CUDA(cudaMemsetAsync(g->counter, 0, sizeof(int32_t), st));
+    if (g->n_items == 0) return FFT_OK;
+#define FFT_LAUNCH(DTV, GV) apply_kernel<MODE, DTV, GV><<<ctas, APPLY_THREADS, smem, st>>>(P)
+    if (g->dt_mode == FFT_DT_STABLE) {
+        if (g->guard) FFT_LAUNCH(FFT_DT_STABLE, true); else FFT_LAUNCH(FFT_DT_STABLE, false);
+    } else if (g->dt_mode == FFT_DT_NAIVE) {
+        if (g->guard) FFT_LAUNCH(FFT_DT_NAIVE, true); else FFT_LAUNCH(FFT_DT_NAIVE, false);
+    } else {
+        FFT_LAUNCH(FFT_DT_FP64, false);
+    }
+#undef FFT_LAUNCH
+    FFT_CUDA(cudaGetLastError());
+    return FFT_OK;
+}
+
+fft_status launch_J(fft_geom g, const float* m, float* d, cudaStream_t st) {
+    ApplyParams P = make_params(g);
+    P.vin = m;
+    P.vout = g->jpart;
+    fft_status rc = launch_mode<MODE_J>(g, P, st);
+    if (rc != FFT_OK) return rc;
+    if (g->M > 0) {
+        int64_t blocks = ceil_div(g->M, 256);
+        j_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->row_off, g->row_ent, g->jpart, g->M, d);
+        FFT_CUDA(cudaGetLastError());
+    }
+    return FFT_OK;
+}
+
+fft_status launch_JT(fft_geom g, const float* din, float* gout, cudaStream_t st) {
+    ApplyParams P = make_params(g);
+    P.vin = din;
+    P.vout = gout;
+    fft_status rc = launch_mode<MODE_JT>(g, P, st);
+    if (rc != FFT_OK) return rc;
+    int64_t blocks = ceil_div(g->V, 256);
+    jt_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->tile_slot0, g->tile_nslot, g->gpart, g->grid.nx,
+                                                       g->grid.ny, g->grid.nz, g->tiles[0], g->tiles[1], gout);
+    FFT_CUDA(cudaGetLastError());
+    return FFT_OK;
+}
+
+fft_status count_support(fft_geom g, int64_t* out) {
+    ApplyParams P = make_params(g);
+    unsigned long long* d_cnt = nullptr;
+    FFT_CUDA(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
+    FFT_CUDA(cudaMemset(d_cnt, 0, sizeof(unsigned long long)));
+    P.icount = d_cnt;
+    fft_status rc = launch_mode<MODE_COUNT>(g, P, 0);
+    unsigned long long h = 0;
+    if (rc == FFT_OK) {
+        cudaError_t e = cudaMemcpy(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "count_support");
+    }
+    cudaFree(d_cnt);
+    *out = (int64_t)h;
+    return rc;
+}
+
+fft_status compute_frob2(fft_geom g, double* out) {
+    ApplyParams P = make_params(g);
+    double* d_sum = nullptr;
+    size_t n = (size_t)(g->n_items > 0 ? g->n_items : 1) * APPLY_WARPS;
+    FFT_CUDA(cudaMalloc(&d_sum, n * sizeof(double)));
+    FFT_CUDA(cudaMemset(d_sum, 0, n * sizeof(double)));
+    P.dsum = d_sum;
+    fft_status rc = launch_mode<MODE_FROB>(g, P, 0);
+    std::vector<double> h(n, 0.0);
+    if (rc == FFT_OK) {
+        cudaError_t e = cudaMemcpy(h.data(), d_sum, n * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "frob2");
+    }
+    cudaFree(d_sum);
+    double s = 0.0;
+    for (size_t i = 0; i < n; ++i) s += h[i];
+    *out = s;
+    return rc;
+}
+
+}  // namespace fftgb
+
+using namespace fftgb;
+
+extern "C" fft_status fft_J_apply(fft_geom g, const float* m_dev, float* d_dev, void* stream) {
+    FFT_ARG(g && m_dev && d_dev, "fft_J_apply: null argument");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    return launch_J(g, m_dev, d_dev, (cudaStream_t)stream);
+}
+
+extern "C" fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev, void* stream) {
+    FFT_ARG(g && d_dev && g_dev, "fft_JT_apply: null argument");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    return launch_JT(g, d_dev, g_dev, (cudaStream_t)stream);
+}
+
+extern "C" fft_status fft_frob2(fft_geom g, double* out) {
+    FFT_ARG(g && out, "fft_frob2: null argument");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    if (g->frob2 < 0.0) {
+        double v = 0.0;
+        rc = compute_frob2(g, &v);
+        if (rc != FFT_OK) return rc;
+        g->frob2 = v;
+    }
+    *out = g->frob2;
+    return FFT_OK;
+}

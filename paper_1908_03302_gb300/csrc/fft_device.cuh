@@ -1,0 +1,93 @@
+// Device-side building blocks of the J / J^T evaluation (Sec. II-C, Eq. Kernel_freq).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_common.cuh"
+
+namespace fftgb {
+
+// 1.5 * 2^23: adding it to a float in [0, 2^22) leaves the integer part in the low mantissa bits.
+constexpr float MAGIC = 12582912.0f;
+constexpr uint32_t MAGIC_BITS_X8 = 0x4B400000u << 3;   // wraps modulo 2^32 on purpose
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Conservative test: may the row's support {R < 1} (band units) reach a box of voxel
+// centres with centre c and half extents hx, hy, hz? R(x) = |x - xs| + |x - xr| - 2 hl is
+// convex, so R(x) >= R(c) + grad R(c) . (x - c) >= R(c) - sum_k |dR/dx_k(c)| half_k over the
+// box. d = c - o is the centre relative to the pair midpoint, e the unit pair axis.
+__device__ __forceinline__ bool box_may_touch(float dx, float dy, float dz, float ex, float ey,
+                                              float ez, float hl, float hx, float hy, float hz) {
+    float sx = dx + hl * ex, sy = dy + hl * ey, sz = dz + hl * ez;   // c - xs
+    float rx = dx - hl * ex, ry = dy - hl * ey, rz = dz - hl * ez;   // c - xr
+    float Rs = sqrtf(sx * sx + sy * sy + sz * sz);
+    float Rr = sqrtf(rx * rx + ry * ry + rz * rz);
+    if (!(Rs > 1e-6f) || !(Rr > 1e-6f)) return true;
+    float is = 1.0f / Rs, ir = 1.0f / Rr;
+    float gx = sx * is + rx * ir, gy = sy * is + ry * ir, gz = sz * is + rz * ir;
+    float lb = (Rs + Rr - 2.0f * hl) - (fabsf(gx) * hx + fabsf(gy) * hy + fabsf(gz) * hz);
+    return !(lb >= 1.0f + CULL_MARGIN);   // NaN keeps the entry
+}
+
+// Normalised detour v = R / U in [0, 1] (saturated) and the two inverse distances, from
+// the pair-frame coordinates of a voxel centre: p = (x - o).e, q2 = |(x - o) x e|^2.
+//   STABLE: R = q2 (A + B) / (A B) + E with A = R_xs + |p + hl|, B = R_xr + |p - hl| and
+//           E = (|p + hl| - (p + hl)) + (|p - hl| + (p - hl)); every term is >= 0, so there
+//           is no cancellation near the ray (R_xs - |ps| = q2 / (R_xs + |ps|)).
+//   NAIVE:  R = R_xs + R_xr - 2 hl by subtraction.
+template <int DT, bool GUARD>
+__device__ __forceinline__ float detour_v(float p, float q2, float hl, float& is, float& ir) {
+    float ps = p + hl, pr = p - hl;
+    float ss = fmaf(ps, ps, q2), rr = fmaf(pr, pr, q2);
+    if (GUARD) {
+        ss = fmaxf(ss, 1e-30f);
+        rr = fmaxf(rr, 1e-30f);
+    }
+    is = rsqrt_approx(ss);
+    ir = rsqrt_approx(rr);
+    if (DT == FFT_DT_NAIVE) {
+        return __saturatef(fmaf(ss, is, fmaf(rr, ir, -2.0f * hl)));
+    } else {
+        float Rs = ss * is, Rr = rr * ir;
+        float aps = fabsf(ps), apr = fabsf(pr);
+        float A = Rs + aps, B = Rr + apr;
+        float N = q2 * (A + B);
+        float rP = rcp_approx(A * B);
+        float E = (aps - ps) + (apr + pr);
+        return __saturatef(fmaf(N, rP, E));
+    }
+}
+
+// Table lookup with linear interpolation: Phi(v) for v in [0, 1], tb the shared-memory byte
+// address of the band table minus (MAGIC bits << 3); nm1 = n_tab - 1. floor(v nm1) comes
+// from a round-down add of MAGIC, whose bit pattern then indexes the table directly.
+__device__ __forceinline__ float phi_lookup(float v, uint32_t tb, float nm1) {
+    float tt = __fmaf_rd(v, nm1, MAGIC);
+    float fr = fmaf(v, nm1, MAGIC - tt);
+    float2 T = lds_f2(tb + (__float_as_uint(tt) << 3));
+    return fmaf(fr, T.y, T.x);
+}
+
+}  // namespace fftgb
