@@ -177,6 +177,26 @@ fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
                          const int32_t* subset_off, int32_t n_subsets,
                          const int32_t* subset_rows, int32_t mode, float* out_dev, void* stream);
 
+/*
+ * fft_psf_noalloc - one point-spread function H_S e_k (a single spike k, a single row subset
+ * S) computed without allocating any device memory. The paper has no counterpart: this entry
+ * point is for callers that must not call the device allocator while they run, such as a
+ * service that reserves its device memory up front or code inside another framework's memory
+ * pool, where a cudaMalloc (which may also synchronise the device) is not allowed.
+ *   spike_vox  voxel index of the unit spike, 0 <= spike_vox < V.
+ *   rows_dev   DEVICE int32[n_rows]: the rows of S (any order). Indices outside [0, M) are
+ *              skipped; the call then returns FFT_ERR_ARG after finishing.
+ *   out_dev    device float32[V], written entirely: out[v] = sum_{p in S} J[p, v] J[p, spike_vox].
+ * Scratch is a fixed array inside the library: 4,194,304 floats plus 256 bytes (about 16 MB),
+ * held by every GPU that loads the library until the process exits. Geometries with more than
+ * 4,194,304 rows are rejected with FFT_ERR_ARG. The first call on each device looks up the
+ * array's device address, so make that first call before any stream capture. All calls share
+ * the array (each clears what it uses); calls that overlap on the GPU race, so serialise them.
+ * Synchronises with `stream` before returning.
+ */
+fft_status fft_psf_noalloc(fft_geom g, int64_t spike_vox, const int32_t* rows_dev, int32_t n_rows,
+                           float* out_dev, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* fft_last_error(void);
 

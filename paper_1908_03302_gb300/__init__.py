@@ -195,6 +195,19 @@ class Geometry:
                                         _stream_handle(stream)))
         return out.view(len(subsets), len(sp), self.V)
 
+    def psf_noalloc(self, spike: int, rows_dev, out=None, stream=None):
+        """One PSF (spike, row subset given as a device int32 tensor) with no device allocation
+        inside the library; the result tensor is allocated here unless `out` is given."""
+        torch = _torch()
+        if not (isinstance(rows_dev, torch.Tensor) and rows_dev.is_cuda and rows_dev.dtype == torch.int32
+                and rows_dev.is_contiguous()):
+            raise TypeError("rows_dev must be a contiguous int32 CUDA tensor")
+        if out is None:
+            out = torch.empty(self.V, device=rows_dev.device, dtype=torch.float32)
+        check(_lib.load().fft_psf_noalloc(self.handle, int(spike), int(rows_dev.data_ptr()), int(rows_dev.numel()),
+                                          _dev_ptr(out, self.V, "out"), _stream_handle(stream)))
+        return out
+
     def close(self):
         if getattr(self, "handle", None) and self.handle.value:
             _lib.load().fft_geom_destroy(self.handle)
