@@ -204,6 +204,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=1024)
     ap.add_argument("--cpu-rows", type=int, default=4096)
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply"],
+                    help="apply: only build the geometry and run --steps J^T and J applications "
+                         "(a short program for ncu captures; prints timings, not the bench line)")
     args = ap.parse_args()
 
     ws, rank, local = dist_setup()
@@ -242,6 +245,25 @@ def main():
     def step(mbuf):
         mbuf.zero_()
         geo.cg_solve(d, w.lambda_rel, n_iter, m=mbuf)
+
+    if args.mode == "apply":
+        r0 = torch.randn(geo.M, device=dev, dtype=torch.float32) * 1e-8
+        g0 = torch.empty(geo.V, device=dev, dtype=torch.float32)
+        for i in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            geo.JT(r0, out=g0)
+            b.record(stream)
+            c, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c.record(stream)
+            geo.J(m_true, out=d)
+            e.record(stream)
+            torch.cuda.synchronize()
+            if rank == 0:
+                print(json.dumps({"apply": i, "ms_JT": a.elapsed_time(b), "ms_J": c.elapsed_time(e),
+                                  "support": support, "evaluated": int(info.evaluated_evals),
+                                  "entries": int(info.n_entries), "items": int(info.n_items)}), flush=True)
+        return 0
 
     for _ in range(args.warmup):
         step(m)
@@ -343,7 +365,8 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded ring-array workload; FP32 kernels, FP64 CG scalars)",
         "config": {"workload": w.name, "pairs": geo.M, "voxels": geo.V, "cg_iters": n_iter,
-                   "support_evals_per_apply": support, "dt_mode": ["stable", "naive", "fp64"][args.dt_mode],
+                   "support_evals_per_apply": support, "evaluated_evals_per_apply": int(info.evaluated_evals),
+                   "dt_mode": ["stable", "naive", "fp64"][args.dt_mode],
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
         "ms_per_cg_iter": total_ms / args.steps / n_iter,
         "ms_per_J": 1e3 * j_avg, "ms_per_JT": 1e3 * jt_avg,

@@ -123,6 +123,7 @@ typedef struct {
                                 of one J or J^T (counted on the device at creation) */
     int64_t scratch_bytes;   /* device bytes owned by the handle */
     int32_t dt_mode;
+    int64_t evaluated_evals; /* (row, voxel) evaluations one apply performs after culling */
 } fft_geom_info_t;
 fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info);
 

@@ -54,7 +54,8 @@ class fft_grid(ctypes.Structure):
 class fft_geom_info_t(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("n_vox", ctypes.c_int64), ("n_entries", ctypes.c_int64),
                 ("n_items", ctypes.c_int64), ("support_evals", ctypes.c_int64),
-                ("scratch_bytes", ctypes.c_int64), ("dt_mode", ctypes.c_int32)]
+                ("scratch_bytes", ctypes.c_int64), ("dt_mode", ctypes.c_int32),
+                ("evaluated_evals", ctypes.c_int64)]
 
 
 # (name, restype, argtypes) for every function declared in include/fft_gb300.h

@@ -37,6 +37,7 @@ struct ApplyParams {
     int n_tab;
     const BandConst* bc;     // device [n_bands]
     const int32_t* tile_rows;
+    const float4* ebase;     // [E] pair-frame coordinates of each entry's tile origin
     const Item* items;
     int n_items;
     int32_t* counter;
@@ -89,87 +90,85 @@ __device__ __forceinline__ float detour_v64(const RowRec64& r, double ox, double
 }
 
 template <int MODE, int DT, bool GUARD>
-__global__ void __launch_bounds__(APPLY_THREADS, 2) apply_kernel(const __grid_constant__ ApplyParams P) {
+__global__ void __launch_bounds__(APPLY_THREADS, 3) apply_kernel(const __grid_constant__ ApplyParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* s_tab = reinterpret_cast<float2*>(smem);
     const int tab_len = P.n_bands * P.n_tab;
     float4* s_stage = reinterpret_cast<float4*>(smem + (((size_t)tab_len * sizeof(float2) + 15) & ~(size_t)15));
-    __shared__ int s_item;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < tab_len; i += APPLY_THREADS) s_tab[i] = P.tab[i];
+    __syncthreads();   // the only CTA-wide barrier: from here on every warp runs on its own
 
     const uint32_t tab_addr = smem_addr(s_tab);
     const float nm1 = (float)(P.n_tab - 1);
-    const int wx = warp & 1, wy = (warp >> 1) & 1, wz = warp >> 2;
     const int lx = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
-    // lane voxel offsets in the tile (sub-brick 0, first of its 4 x voxels)
-    const int oxi = 8 * wx + 4 * lx, oyi = 8 * wy + ly, ozi = 4 * wz + lz;
-    const float Xl = (float)oxi, Yl = (float)oyi, Zl = (float)ozi;
     float4* stg = s_stage + warp * 96;
+    const int n_units = P.n_items * APPLY_WARPS;
 
     for (;;) {
-        __syncthreads();
-        if (tid == 0) s_item = atomicAdd(P.counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= P.n_items) break;
+        // A unit is one 8 x 8 x 4 region of one item (unit = item * 8 + region).
+        int unit = 0;
+        if (lane == 0) unit = atomicAdd(P.counter, 1);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        if (unit >= n_units) break;
+        const int it = unit >> 3, region = unit & 7;
         const Item item = P.items[it];
         const int tx = item.tile % P.tiles_x;
         const int ty = (item.tile / P.tiles_x) % P.tiles_y;
         const int tz = item.tile / (P.tiles_x * P.tiles_y);
         const int TX = TILE_X * tx, TY = TILE_Y * ty, TZ = TILE_Z * tz;
+        const int wx = region & 1, wy = (region >> 1) & 1, wz = region >> 2;
+        // lane voxel offsets in the tile (sub-brick 0, first of its 4 x voxels)
+        const int oxi = 8 * wx + 4 * lx, oyi = 8 * wy + ly, ozi = 4 * wz + lz;
+        const float Xl = (float)oxi, Yl = (float)oyi, Zl = (float)ozi;
 
-        // validity of this lane's voxels and of the warp's sub-bricks
-        const bool zin = (TZ + ozi) < P.nz;
-        bool vin_[2][NX_LANE];
-        int64_t vidx[2];
+        // validity of this lane's voxels (bit 4 s + t) and of the region's sub-bricks
+        uint32_t vmask = 0;
+        if (TZ + ozi < P.nz) {
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int y = TY + oyi + 4 * s;
-            vidx[s] = ((int64_t)(TZ + ozi) * P.ny + y) * P.nx + TX + oxi;
+            for (int s = 0; s < 2; ++s)
 #pragma unroll
-            for (int t = 0; t < NX_LANE; ++t) vin_[s][t] = zin && (y < P.ny) && (TX + oxi + t < P.nx);
+                for (int t = 0; t < NX_LANE; ++t)
+                    if (TY + oyi + 4 * s < P.ny && TX + oxi + t < P.nx) vmask |= 1u << (4 * s + t);
         }
+        const int64_t vbase = ((int64_t)(TZ + ozi) * P.ny + TY + oyi) * P.nx + TX + oxi;
         const bool sub_ok0 = (TX + 8 * wx < P.nx) && (TY + 8 * wy < P.ny) && (TZ + 4 * wz < P.nz);
         const bool sub_ok1 = (TX + 8 * wx < P.nx) && (TY + 8 * wy + 4 < P.ny) && (TZ + 4 * wz < P.nz);
 
         float acc[2][NX_LANE];
         float mv[2][NX_LANE];
         double dacc = 0.0;
-        unsigned long long cnt = 0;
+        unsigned long long cnt = 0, cnt_eval = 0;
 #pragma unroll
         for (int s = 0; s < 2; ++s)
 #pragma unroll
             for (int t = 0; t < NX_LANE; ++t) {
                 acc[s][t] = 0.0f;
                 mv[s][t] = 0.0f;
-                if (MODE == MODE_J && vin_[s][t]) mv[s][t] = __ldg(P.vin + vidx[s] + t);
+                if (MODE == MODE_J && ((vmask >> (4 * s + t)) & 1u))
+                    mv[s][t] = __ldg(P.vin + vbase + (int64_t)(4 * s) * P.nx + t);
             }
 
         for (int64_t e0 = item.e0; e0 < item.e1; e0 += 32) {
             // ---- stage: lane l prepares row e0 + l
             const int64_t e = e0 + lane;
             const bool have = e < item.e1;
-            bool ok0 = false, ok1 = false;
+            bool ok0 = false, ok1 = false, in0 = false, in1 = false;
             if (have) {
                 const int p = P.tile_rows[e];
+                const float4 base = P.ebase[e];
                 const RowRec r = P.rec[p];
                 const int b = P.row_band[p];
                 const BandConst bc = P.bc[b];
                 const float hb = bc.h;
                 float W = r.b.w;
                 if (MODE == MODE_JT) W *= __ldg(P.vin + p);
+                const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
+                // sub-brick centres relative to the pair midpoint (FP32; used by the bound only)
                 const float dx = fmaf((float)TX, hb, bc.org[0]) - r.a.x;
                 const float dy = fmaf((float)TY, hb, bc.org[1]) - r.a.y;
                 const float dz = fmaf((float)TZ, hb, bc.org[2]) - r.a.z;
-                const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
-                const float pT = fmaf(dx, ex, fmaf(dy, ey, dz * ez));
-                const float c1T = fmaf(dy, ez, -dz * ey);
-                const float c2T = fmaf(dz, ex, -dx * ez);
-                const float c3T = fmaf(dx, ey, -dy * ex);
-                const float hx = hb * ex, hy = hb * ey, hz = hb * ez;
-                // sub-brick centres relative to the pair midpoint
                 const float cx = fmaf(8.0f * wx + 3.5f, hb, dx);
                 const float cz = fmaf(4.0f * wz + 1.5f, hb, dz);
                 const float cy0 = fmaf(8.0f * wy + 1.5f, hb, dy);
@@ -179,13 +178,20 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) apply_kernel(const __grid_co
                 const bool live = (MODE != MODE_JT) || (W != 0.0f);
                 ok0 = live && sub_ok0 && box_may_touch(cx, cy0, cz, ex, ey, ez, hl, hxx, hyy, hyy);
                 ok1 = live && sub_ok1 && box_may_touch(cx, cy1, cz, ex, ey, ez, hl, hxx, hyy, hyy);
+                // sub-bricks whose voxels all satisfy |p| <= hl (between the transducer planes)
+                const float pext = hxx * fabsf(ex) + hyy * (fabsf(ey) + fabsf(ez)) + 1e-3f;
+                const float pcx = fmaf(cx, ex, cz * ez);
+                in0 = fabsf(fmaf(cy0, ey, pcx)) + pext <= hl;
+                in1 = fabsf(fmaf(cy1, ey, pcx)) + pext <= hl;
                 const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
-                stg[lane * 3 + 0] = make_float4(pT, c1T, c2T, c3T);
-                stg[lane * 3 + 1] = make_float4(hx, hy, hz, hl);
+                stg[lane * 3 + 0] = base;
+                stg[lane * 3 + 1] = make_float4(hb * ex, hb * ey, hb * ez, hl);
                 stg[lane * 3 + 2] = make_float4(W, __uint_as_float(tb), __int_as_float(p), __int_as_float(b));
             }
             const uint32_t m0 = __ballot_sync(0xffffffffu, ok0);
             const uint32_t m1 = __ballot_sync(0xffffffffu, ok1);
+            const uint32_t i0 = __ballot_sync(0xffffffffu, in0);
+            const uint32_t i1 = __ballot_sync(0xffffffffu, in1);
             __syncwarp();
             uint32_t mm = m0 | m1;
             float mypart = 0.0f;
@@ -213,35 +219,47 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) apply_kernel(const __grid_co
                     }
                     if (!((ms >> bit) & 1u)) continue;
                     const float c1sq = c1 * c1;
-#pragma unroll
-                    for (int t = 0; t < NX_LANE; ++t) {
-                        const float ft = (float)t;
-                        float is, ir, v, w;
-                        if (DT == FFT_DT_FP64) {
-                            const RowRec64 r64 = P.rec64[__float_as_int(C.z)];
-                            const int b = __float_as_int(C.w);
-                            v = detour_v64(r64, P.org[0], P.org[1], P.org[2], P.h, TX + oxi + t,
-                                           TY + oyi + 4 * s, TZ + ozi, P.bc[b].U, w);
-                            is = 1.0f;
-                            ir = w;
-                        } else {
-                            const float pt = fmaf(ft, hx, pb);
-                            const float c2t = fmaf(-ft, hz, c2);
-                            const float c3t = fmaf(ft, hy, c3);
-                            const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
-                            v = detour_v<DT, GUARD>(pt, q2, hl, is, ir);
-                        }
-                        if (MODE == MODE_COUNT) {
-                            if (vin_[s][t] && v < 1.0f) ++cnt;
-                            continue;
-                        }
-                        const float val = phi_lookup(v, tb, nm1) * (is * ir);
-                        if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);
-                        if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);
-                        if (MODE == MODE_FROB) {
-                            if (vin_[s][t]) part = fmaf(val, val, part);
-                        }
+                    const float psb = pb + hl, prb = pb - hl;
+                    const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
+#define FFT_EVAL_SUB(INNER_V)                                                                        \
+    _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                          \
+        const float ft = (float)t;                                                                 \
+        float is, ir, v, w;                                                                        \
+        if (DT == FFT_DT_FP64) {                                                                   \
+            const RowRec64 r64 = P.rec64[__float_as_int(C.z)];                                     \
+            const int b = __float_as_int(C.w);                                                     \
+            v = detour_v64(r64, P.org[0], P.org[1], P.org[2], P.h, TX + oxi + t, TY + oyi + 4 * s, \
+                           TZ + ozi, P.bc[b].U, w);                                                \
+            is = 1.0f;                                                                             \
+            ir = w;                                                                                \
+        } else {                                                                                   \
+            const float pst = fmaf(ft, hx, psb);                                                   \
+            const float prt = fmaf(ft, hx, prb);                                                   \
+            const float c2t = fmaf(-ft, hz, c2);                                                   \
+            const float c3t = fmaf(ft, hy, c3);                                                    \
+            const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                 \
+            v = detour_v<DT, GUARD, INNER_V>(pst, prt, q2, hl, is, ir);                            \
+        }                                                                                          \
+        if (MODE == MODE_COUNT) {                                                                  \
+            if ((vmask >> (4 * s + t)) & 1u) {                                                     \
+                ++cnt_eval;                                                                        \
+                if (v < 1.0f) ++cnt;                                                               \
+            }                                                                                      \
+            continue;                                                                              \
+        }                                                                                          \
+        const float val = phi_lookup(v, tb, nm1) * (is * ir);                                      \
+        if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                                  \
+        if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                      \
+        if (MODE == MODE_FROB) {                                                                   \
+            if ((vmask >> (4 * s + t)) & 1u) part = fmaf(val, val, part);                          \
+        }                                                                                          \
+    }
+                    if (inner) {
+                        FFT_EVAL_SUB(true)
+                    } else {
+                        FFT_EVAL_SUB(false)
                     }
+#undef FFT_EVAL_SUB
                 }
                 if (MODE == MODE_J) {
                     part = warp_sum(part);
@@ -249,7 +267,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) apply_kernel(const __grid_co
                 }
                 if (MODE == MODE_FROB) dacc += (double)part * (double)W * (double)W;
             }
-            if (MODE == MODE_J && have) P.vout[e * 8 + warp] = mypart;
+            if (MODE == MODE_J && have) P.vout[e * 8 + region] = mypart;
             __syncwarp();
         }
 
@@ -259,7 +277,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) apply_kernel(const __grid_co
                 if (item.slot < 0) {
 #pragma unroll
                     for (int t = 0; t < NX_LANE; ++t)
-                        if (vin_[s][t]) P.vout[vidx[s] + t] = acc[s][t];
+                        if ((vmask >> (4 * s + t)) & 1u) P.vout[vbase + (int64_t)(4 * s) * P.nx + t] = acc[s][t];
                 } else {
                     // local index inside the tile: (z * 16 + y) * 16 + x
                     const int loc = ((ozi * TILE_Y) + oyi + 4 * s) * TILE_X + oxi;
@@ -270,13 +288,18 @@ __global__ void __launch_bounds__(APPLY_THREADS, 2) apply_kernel(const __grid_co
         }
         if (MODE == MODE_FROB) {
             dacc = warp_sum_d(dacc);
-            if (lane == 0) P.dsum[(int64_t)it * APPLY_WARPS + warp] = dacc;
+            if (lane == 0) P.dsum[unit] = dacc;
         }
         if (MODE == MODE_COUNT) {
-            unsigned long long c = cnt;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-            if (lane == 0 && c) atomicAdd(P.icount, c);
+            for (int o = 16; o > 0; o >>= 1) {
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                cnt_eval += __shfl_xor_sync(0xffffffffu, cnt_eval, o);
+            }
+            if (lane == 0) {
+                if (cnt) atomicAdd(P.icount, cnt);
+                if (cnt_eval) atomicAdd(P.icount + 1, cnt_eval);
+            }
         }
     }
 }
@@ -327,6 +350,7 @@ static ApplyParams make_params(fft_geom g) {
     P.n_tab = g->n_tab;
     P.bc = g->d_band;
     P.tile_rows = g->tile_rows;
+    P.ebase = g->ebase;
     P.items = g->items;
     P.n_items = g->n_items;
     P.counter = g->counter;
@@ -436,27 +460,29 @@ fft_status launch_JT(fft_geom g, const float* din, float* gout, cudaStream_t st)
     return FFT_OK;
 }
 
-fft_status count_support(fft_geom g, int64_t* out) {
+// In-support evaluations (dt < dt_max) of one apply and evaluations actually performed.
+fft_status count_support(fft_geom g, int64_t* support, int64_t* evaluated) {
     ApplyParams P = make_params(g);
     unsigned long long* d_cnt = nullptr;
-    FFT_CUDA(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
-    FFT_CUDA(cudaMemset(d_cnt, 0, sizeof(unsigned long long)));
+    FFT_CUDA(cudaMalloc(&d_cnt, 2 * sizeof(unsigned long long)));
+    FFT_CUDA(cudaMemset(d_cnt, 0, 2 * sizeof(unsigned long long)));
     P.icount = d_cnt;
     fft_status rc = launch_mode<MODE_COUNT>(g, P, 0);
-    unsigned long long h = 0;
+    unsigned long long h[2] = {0, 0};
     if (rc == FFT_OK) {
-        cudaError_t e = cudaMemcpy(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpy(h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = cuda_fail(e, "count_support");
     }
     cudaFree(d_cnt);
-    *out = (int64_t)h;
+    *support = (int64_t)h[0];
+    *evaluated = (int64_t)h[1];
     return rc;
 }
 
 fft_status compute_frob2(fft_geom g, double* out) {
     ApplyParams P = make_params(g);
     double* d_sum = nullptr;
-    size_t n = (size_t)(g->n_items > 0 ? g->n_items : 1) * APPLY_WARPS;
+    size_t n = (size_t)(g->n_items > 0 ? g->n_items : 1) * APPLY_WARPS;   // one per unit
     FFT_CUDA(cudaMalloc(&d_sum, n * sizeof(double)));
     FFT_CUDA(cudaMemset(d_sum, 0, n * sizeof(double)));
     P.dsum = d_sum;

@@ -103,6 +103,7 @@ struct fft_geom_s {
     int64_t E = 0;                       // entries
     int64_t* tile_off = nullptr;         // [n_tiles + 1]
     int32_t* tile_rows = nullptr;        // [E]
+    float4* ebase = nullptr;             // [E] (p, c1, c2, c3) of the tile origin in the row's pair frame
     int64_t* row_off = nullptr;          // [M + 1]
     int64_t* row_ent = nullptr;          // [E] tile-major entry ids of each row, ascending
     fftgb::Item* items = nullptr;        // [n_items]
@@ -114,6 +115,7 @@ struct fft_geom_s {
     float* gpart = nullptr;              // [n_slots * TILE_VOX]
     int32_t* counter = nullptr;          // [4] work counters
     int64_t support = 0;
+    int64_t evaluated = 0;
     double frob2 = -1.0;
     int64_t scratch_bytes = 0;
     int apply_ctas = 0;
@@ -140,7 +142,7 @@ fft_status launch_J(fft_geom g, const float* m, float* d, cudaStream_t st);
 fft_status launch_JT(fft_geom g, const float* din, float* gout, cudaStream_t st);
 fft_status launch_JT_rows(fft_geom g, const float* din, float* gout, cudaStream_t st);
 fft_status check_device(int dev);
-fft_status count_support(fft_geom g, int64_t* out);
+fft_status count_support(fft_geom g, int64_t* support, int64_t* evaluated);
 fft_status compute_frob2(fft_geom g, double* out);
 fft_status set_apply_attributes(fft_geom g);
 int apply_occupancy(fft_geom g);

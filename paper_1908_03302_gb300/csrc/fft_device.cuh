@@ -57,9 +57,12 @@ __device__ __forceinline__ bool box_may_touch(float dx, float dy, float dz, floa
 //           E = (|p + hl| - (p + hl)) + (|p - hl| + (p - hl)); every term is >= 0, so there
 //           is no cancellation near the ray (R_xs - |ps| = q2 / (R_xs + |ps|)).
 //   NAIVE:  R = R_xs + R_xr - 2 hl by subtraction.
-template <int DT, bool GUARD>
-__device__ __forceinline__ float detour_v(float p, float q2, float hl, float& is, float& ir) {
-    float ps = p + hl, pr = p - hl;
+// INNER: the caller guarantees |p| <= hl (the voxel lies between the planes through the two
+// transducers normal to the pair axis); then E = 0 and the absolute values drop out.
+// The caller passes ps = p + hl and pr = p - hl (the axial offsets from the emitter and the
+// receiver) directly, so that they can be stepped along a run of voxels.
+template <int DT, bool GUARD, bool INNER = false>
+__device__ __forceinline__ float detour_v(float ps, float pr, float q2, float hl, float& is, float& ir) {
     float ss = fmaf(ps, ps, q2), rr = fmaf(pr, pr, q2);
     if (GUARD) {
         ss = fmaxf(ss, 1e-30f);
@@ -69,10 +72,13 @@ __device__ __forceinline__ float detour_v(float p, float q2, float hl, float& is
     ir = rsqrt_approx(rr);
     if (DT == FFT_DT_NAIVE) {
         return __saturatef(fmaf(ss, is, fmaf(rr, ir, -2.0f * hl)));
+    } else if (INNER) {
+        float A = fmaf(ss, is, ps), B = fmaf(rr, ir, -pr);
+        float N = q2 * (A + B);
+        return __saturatef(N * rcp_approx(A * B));
     } else {
-        float Rs = ss * is, Rr = rr * ir;
         float aps = fabsf(ps), apr = fabsf(pr);
-        float A = Rs + aps, B = Rr + apr;
+        float A = fmaf(ss, is, aps), B = fmaf(rr, ir, apr);   // R_xs + |ps|, R_xr + |pr|
         float N = q2 * (A + B);
         float rP = rcp_approx(A * B);
         float E = (aps - ps) + (apr + pr);

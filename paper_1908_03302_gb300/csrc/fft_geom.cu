@@ -84,6 +84,37 @@ __global__ void tile_fill_kernel(const CullParams C, const int64_t* __restrict__
     }
 }
 
+// FP64 pair-frame coordinates of each entry's tile origin (voxel (TX, TY, TZ) centre) in band
+// units: p = (x_T - o).e and c = (x_T - o) x e. Computing them here in double precision keeps
+// the large (~L/2) coordinates out of FP32 arithmetic; the kernels add only small offsets.
+__global__ void entry_base_kernel(const int64_t* __restrict__ off, const int32_t* __restrict__ rows_of_entry,
+                                  const double* __restrict__ tx, const int32_t* __restrict__ pairs,
+                                  const int32_t* __restrict__ row_band, const BandConst* __restrict__ bc,
+                                  double ox, double oy, double oz, double h, int tiles_x, int tiles_y,
+                                  float4* __restrict__ ebase) {
+    const int T = blockIdx.x;
+    const int tx_ = T % tiles_x, ty_ = (T / tiles_x) % tiles_y, tz_ = T / (tiles_x * tiles_y);
+    const double xT = ox + (double)(TILE_X * tx_) * h;
+    const double yT = oy + (double)(TILE_Y * ty_) * h;
+    const double zT = oz + (double)(TILE_Z * tz_) * h;
+    for (int64_t e = off[T] + threadIdx.x; e < off[T + 1]; e += blockDim.x) {
+        const int p = rows_of_entry[e];
+        const double* xs = tx + 3 * (int64_t)pairs[2 * p];
+        const double* xr = tx + 3 * (int64_t)pairs[2 * p + 1];
+        const double U = bc[row_band[p]].U;
+        double ax = xr[0] - xs[0], ay = xr[1] - xs[1], az = xr[2] - xs[2];
+        const double L = sqrt(ax * ax + ay * ay + az * az);
+        ax /= L;
+        ay /= L;
+        az /= L;
+        const double dx = (xT - 0.5 * (xs[0] + xr[0])) / U;
+        const double dy = (yT - 0.5 * (xs[1] + xr[1])) / U;
+        const double dz = (zT - 0.5 * (xs[2] + xr[2])) / U;
+        ebase[e] = make_float4((float)(dx * ax + dy * ay + dz * az), (float)(dy * az - dz * ay),
+                               (float)(dz * ax - dx * az), (float)(dx * ay - dy * ax));
+    }
+}
+
 __global__ void row_count_kernel(const int32_t* __restrict__ tile_rows, int64_t E, int32_t* __restrict__ cnt) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < E) atomicAdd(&cnt[tile_rows[e]], 1);
@@ -142,7 +173,7 @@ fft_status dmalloc(fft_geom g, T** p, size_t count) {
 
 void free_geom(fft_geom g) {
     if (!g) return;
-    void* ptrs[] = {g->d_band, g->rec, g->rec64, g->row_band, g->tab, g->tile_off, g->tile_rows,
+    void* ptrs[] = {g->d_band, g->rec, g->rec64, g->row_band, g->tab, g->tile_off, g->tile_rows, g->ebase,
                     g->row_off, g->row_ent, g->items, g->tile_slot0, g->tile_nslot, g->jpart,
                     g->gpart, g->counter, g->cg_r, g->cg_q, g->cg_s, g->cg_p, g->cg_d, g->cg_m,
                     g->cg_scal, g->cg_dots, g->cg_status, g->cg_hist};
@@ -347,6 +378,28 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
         GEOM_CUDA(cudaGetLastError());
     }
 
+    // ---- FP64 pair-frame bases of the entries
+    GEOM_TRY(dmalloc(g, &g->ebase, g->E));
+    if (g->E > 0) {
+        double* d_tx = nullptr;
+        int32_t* d_pairs = nullptr;
+        cudaError_t e = cudaMalloc(&d_tx, sizeof(double) * 3 * n_tx);
+        if (e == cudaSuccess) e = cudaMalloc(&d_pairs, sizeof(int32_t) * 2 * n_rows);
+        if (e == cudaSuccess) e = cudaMemcpy(d_tx, tx_xyz, sizeof(double) * 3 * n_tx, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_pairs, rows, sizeof(int32_t) * 2 * n_rows, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            entry_base_kernel<<<(unsigned)g->n_tiles, 256>>>(g->tile_off, g->tile_rows, d_tx, d_pairs, g->row_band,
+                                                             g->d_band, grid->origin[0], grid->origin[1],
+                                                             grid->origin[2], grid->h, g->tiles[0], g->tiles[1],
+                                                             g->ebase);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(d_tx);
+        cudaFree(d_pairs);
+        GEOM_CUDA(e);
+    }
+
     // ---- row-major view of the entries
     {
         int32_t* d_rc = nullptr;
@@ -420,7 +473,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
         GEOM_CUDA(cudaMemcpy(g->tile_nslot, nslot.data(), sizeof(int32_t) * g->n_tiles, cudaMemcpyHostToDevice));
     }
     GEOM_CUDA(cudaDeviceSynchronize());
-    GEOM_TRY(count_support(g, &g->support));
+    GEOM_TRY(count_support(g, &g->support, &g->evaluated));
     GEOM_CUDA(cudaDeviceSynchronize());
 #undef GEOM_TRY
 #undef GEOM_CUDA
@@ -446,6 +499,7 @@ extern "C" fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info) {
     info->n_entries = g->E;
     info->n_items = g->n_items;
     info->support_evals = g->support;
+    info->evaluated_evals = g->evaluated;
     info->scratch_bytes = g->scratch_bytes;
     info->dt_mode = g->dt_mode;
     return FFT_OK;

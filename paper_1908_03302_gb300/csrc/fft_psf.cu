@@ -39,7 +39,7 @@ __global__ void column_kernel(const RowRec* __restrict__ rec, const int32_t* __r
     const float c1 = fmaf(dy, ez, -dz * ey), c2 = fmaf(dz, ex, -dx * ez), c3 = fmaf(dx, ey, -dy * ex);
     const float q2 = fmaf(c1, c1, fmaf(c2, c2, c3 * c3));
     float is, ir;
-    const float vv = detour_v<DT == FFT_DT_NAIVE ? FFT_DT_NAIVE : FFT_DT_STABLE, true>(pp, q2, r.a.w, is, ir);
+    const float vv = detour_v<DT == FFT_DT_NAIVE ? FFT_DT_NAIVE : FFT_DT_STABLE, true>(pp + r.a.w, pp - r.a.w, q2, r.a.w, is, ir);
     const float nm1 = (float)(n_tab - 1);
     const float u = vv * nm1;
     int k = (int)floorf(u);
