@@ -199,7 +199,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ring256", choices=["ring32", "ring256"])
+    ap.add_argument("--workload", default="ring256", choices=["ring32", "ring256", "slices3d"])
     ap.add_argument("--dt-mode", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=1024)
@@ -219,14 +219,14 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = wl.by_name(args.workload)
-    band = w.bands[0]
 
-    # ---- setup (not part of a step): table, geometry, data
+    # ---- setup (not part of a step): tables, geometry, data
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    table = fg.Table(band.f_center_hz, band.f_sigma_hz, band.n_samples, band.dt_max)
+    tables = [fg.Table(b.f_center_hz, b.f_sigma_hz, b.n_samples, b.dt_max) for b in w.bands]
     t1 = time.perf_counter()
-    geo = fg.Geometry(w.tx, w.row_pairs(), w.grid, w.c0, [table], dt_mode=args.dt_mode)
+    geo = fg.Geometry(w.tx, w.row_pairs(), w.grid, w.c0, tables,
+                      band_of_row=w.band_of_row if len(w.bands) > 1 else None, dt_mode=args.dt_mode)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     info = geo.info()

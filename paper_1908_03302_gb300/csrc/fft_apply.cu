@@ -37,7 +37,8 @@ struct ApplyParams {
     int n_tab;
     const BandConst* bc;     // device [n_bands]
     const int32_t* tile_rows;
-    const float4* ebase;     // [E] pair-frame coordinates of each entry's tile origin
+    const float4* ebase;     // [E] (p + hl, p - hl, c1, c2) of each entry's tile origin (pair frame)
+    const float* ebase3;     // [E] c3 of each entry's tile origin
     const Item* items;
     int n_items;
     int32_t* counter;
@@ -89,8 +90,8 @@ __device__ __forceinline__ float detour_v64(const RowRec64& r, double ox, double
     return (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
 }
 
-template <int MODE, int DT, bool GUARD>
-__global__ void __launch_bounds__(APPLY_THREADS, 3) apply_kernel(const __grid_constant__ ApplyParams P) {
+template <int MODE, int DT, bool GUARD, bool SHARP>
+__global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(const __grid_constant__ ApplyParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* s_tab = reinterpret_cast<float2*>(smem);
     const int tab_len = P.n_bands * P.n_tab;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, 3) apply_kernel(const __grid_co
             if (have) {
                 const int p = P.tile_rows[e];
                 const float4 base = P.ebase[e];
+                const float base3 = P.ebase3[e];
                 const RowRec r = P.rec[p];
                 const int b = P.row_band[p];
                 const BandConst bc = P.bc[b];
@@ -185,8 +187,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, 3) apply_kernel(const __grid_co
                 in1 = fabsf(fmaf(cy1, ey, pcx)) + pext <= hl;
                 const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
                 stg[lane * 3 + 0] = base;
-                stg[lane * 3 + 1] = make_float4(hb * ex, hb * ey, hb * ez, hl);
-                stg[lane * 3 + 2] = make_float4(W, __uint_as_float(tb), __int_as_float(p), __int_as_float(b));
+                stg[lane * 3 + 1] = make_float4(hb * ex, hb * ey, hb * ez, base3);
+                stg[lane * 3 + 2] =
+                    make_float4(W, __uint_as_float(tb), __int_as_float(p), __int_as_float(b | (bc.sharp << 8)));
             }
             const uint32_t m0 = __ballot_sync(0xffffffffu, ok0);
             const uint32_t m1 = __ballot_sync(0xffffffffu, ok1);
@@ -201,25 +204,31 @@ __global__ void __launch_bounds__(APPLY_THREADS, 3) apply_kernel(const __grid_co
                 const float4 A = stg[bit * 3 + 0];
                 const float4 B = stg[bit * 3 + 1];
                 const float4 C = stg[bit * 3 + 2];
-                const float hx = B.x, hy = B.y, hz = B.z, hl = B.w, W = C.x;
+                const float hx = B.x, hy = B.y, hz = B.z, W = C.x;
+                const float hl = 0.5f * (A.x - A.y);   // used by the textbook (NAIVE) detour only
                 const uint32_t tb = __float_as_uint(C.y);
-                // lane base (sub-brick 0, t = 0) in the pair frame
-                float pb = fmaf(Xl, hx, fmaf(Yl, hy, fmaf(Zl, hz, A.x)));
-                float c1 = fmaf(Yl, hz, fmaf(-Zl, hy, A.y));
-                float c2 = fmaf(Zl, hx, fmaf(-Xl, hz, A.z));
-                float c3 = fmaf(Xl, hy, fmaf(-Yl, hx, A.w));
+                // voxels whose FP32 detour falls within CUT_BAND of a sharp band's cut-off
+                const float cutb = (SHARP && (__float_as_int(C.w) >> 8)) ? CUT_BAND : -1.0f;
+                uint32_t fix = 0;
+                // lane base (sub-brick 0, t = 0) in the pair frame: small offsets added to the
+                // tile origin's FP64-derived values
+                const float off = fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
+                float psb = A.x + off, prb = A.y + off;
+                float c1 = fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
+                float c2 = fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
+                float c3 = fmaf(Xl, hy, fmaf(-Yl, hx, B.w));
                 float part = 0.0f;
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const uint32_t ms = s ? m1 : m0;
                     if (s == 1) {
-                        pb = fmaf(4.0f, hy, pb);
+                        psb = fmaf(4.0f, hy, psb);
+                        prb = fmaf(4.0f, hy, prb);
                         c1 = fmaf(4.0f, hz, c1);
                         c3 = fmaf(-4.0f, hx, c3);
                     }
                     if (!((ms >> bit) & 1u)) continue;
                     const float c1sq = c1 * c1;
-                    const float psb = pb + hl, prb = pb - hl;
                     const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
 #define FFT_EVAL_SUB(INNER_V)                                                                        \
     _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                          \
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, 3) apply_kernel(const __grid_co
         float is, ir, v, w;                                                                        \
         if (DT == FFT_DT_FP64) {                                                                   \
             const RowRec64 r64 = P.rec64[__float_as_int(C.z)];                                     \
-            const int b = __float_as_int(C.w);                                                     \
+            const int b = __float_as_int(C.w) & 0xff;                                              \
             v = detour_v64(r64, P.org[0], P.org[1], P.org[2], P.h, TX + oxi + t, TY + oyi + 4 * s, \
                            TZ + ozi, P.bc[b].U, w);                                                \
             is = 1.0f;                                                                             \
@@ -238,7 +247,13 @@ __global__ void __launch_bounds__(APPLY_THREADS, 3) apply_kernel(const __grid_co
             const float c2t = fmaf(-ft, hz, c2);                                                   \
             const float c3t = fmaf(ft, hy, c3);                                                    \
             const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                 \
-            v = detour_v<DT, GUARD, INNER_V>(pst, prt, q2, hl, is, ir);                            \
+            if (SHARP) {                                                                           \
+                v = detour_v<DT, GUARD, INNER_V, true>(pst, prt, q2, hl, is, ir);                  \
+                if (fabsf(v - 1.0f) < cutb) fix |= 1u << (4 * s + t);                              \
+                v = __saturatef(v);                                                                \
+            } else {                                                                               \
+                v = detour_v<DT, GUARD, INNER_V>(pst, prt, q2, hl, is, ir);                        \
+            }                                                                                      \
         }                                                                                          \
         if (MODE == MODE_COUNT) {                                                                  \
             if ((vmask >> (4 * s + t)) & 1u) {                                                     \
@@ -260,6 +275,57 @@ __global__ void __launch_bounds__(APPLY_THREADS, 3) apply_kernel(const __grid_co
                         FFT_EVAL_SUB(false)
                     }
 #undef FFT_EVAL_SUB
+                }
+                if (SHARP && DT != FFT_DT_FP64 && __any_sync(0xffffffffu, fix != 0u)) {
+                    // Re-decide dt < dt_max in FP64 for the flagged voxels and correct what the
+                    // FP32 pass added (the FP32 value is recomputed by the same operations).
+                    const int b = __float_as_int(C.w) & 0xff;
+                    const double U = P.bc[b].U;
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+#pragma unroll
+                        for (int t = 0; t < NX_LANE; ++t) {
+                            if (!((fix >> (4 * s + t)) & 1u)) continue;
+                            const float offs = fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
+                            float pss = A.x + offs, prs = A.y + offs;
+                            float c1s = fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
+                            const float c2s = fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
+                            float c3s = fmaf(Xl, hy, fmaf(-Yl, hx, B.w));
+                            if (s == 1) {
+                                pss = fmaf(4.0f, hy, pss);
+                                prs = fmaf(4.0f, hy, prs);
+                                c1s = fmaf(4.0f, hz, c1s);
+                                c3s = fmaf(-4.0f, hx, c3s);
+                            }
+                            const float ft = (float)t;
+                            const float c1sq = c1s * c1s;
+                            const float pst = fmaf(ft, hx, pss);
+                            const float prt = fmaf(ft, hx, prs);
+                            const float c2t = fmaf(-ft, hz, c2s);
+                            const float c3t = fmaf(ft, hy, c3s);
+                            const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
+                            const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
+                            float is, ir;
+                            const float v = __saturatef(inner ? detour_v<DT, GUARD, true, true>(pst, prt, q2, hl, is, ir)
+                                                              : detour_v<DT, GUARD, false, true>(pst, prt, q2, hl, is, ir));
+                            const bool in = in_support64(P.rec64[__float_as_int(C.z)], P.org[0], P.org[1], P.org[2],
+                                                         P.h, TX + oxi + t, TY + oyi + 4 * s, TZ + ozi, U);
+                            const float v2 = settle_cut(v, in);
+                            if (v2 == v) continue;
+                            if (MODE == MODE_COUNT) {
+                                if ((vmask >> (4 * s + t)) & 1u) cnt += (v2 < 1.0f) ? 1ull : ~0ull;
+                                continue;
+                            }
+                            const float w = is * ir;
+                            const float val1 = phi_lookup(v, tb, nm1) * w;
+                            const float val2 = phi_lookup(v2, tb, nm1) * w;
+                            if (MODE == MODE_JT) acc[s][t] = fmaf(val2 - val1, W, acc[s][t]);
+                            if (MODE == MODE_J) part = fmaf(val2 - val1, mv[s][t], part);
+                            if (MODE == MODE_FROB) {
+                                if ((vmask >> (4 * s + t)) & 1u) part += val2 * val2 - val1 * val1;
+                            }
+                        }
+                    }
                 }
                 if (MODE == MODE_J) {
                     part = warp_sum(part);
@@ -351,6 +417,7 @@ static ApplyParams make_params(fft_geom g) {
     P.bc = g->d_band;
     P.tile_rows = g->tile_rows;
     P.ebase = g->ebase;
+    P.ebase3 = g->ebase3;
     P.items = g->items;
     P.n_items = g->n_items;
     P.counter = g->counter;
@@ -374,21 +441,28 @@ size_t apply_smem(fft_geom g) {
     return tab + (size_t)APPLY_WARPS * 96 * sizeof(float4);
 }
 
-template <int MODE, int DT, bool G>
+template <int MODE, int DT, bool G, bool S>
 static fft_status set_attr_one(size_t smem) {
-    FFT_CUDA(cudaFuncSetAttribute(apply_kernel<MODE, DT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FFT_CUDA(cudaFuncSetAttribute(apply_kernel<MODE, DT, G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     return FFT_OK;
+}
+
+template <int MODE, int DT>
+static fft_status set_attr_dt(size_t smem) {
+    fft_status rc;
+    if ((rc = set_attr_one<MODE, DT, false, false>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_one<MODE, DT, true, false>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_one<MODE, DT, false, true>(smem)) != FFT_OK) return rc;
+    return set_attr_one<MODE, DT, true, true>(smem);
 }
 
 template <int MODE>
 static fft_status set_attr_mode(size_t smem) {
     fft_status rc;
-    if ((rc = set_attr_one<MODE, FFT_DT_STABLE, false>(smem)) != FFT_OK) return rc;
-    if ((rc = set_attr_one<MODE, FFT_DT_STABLE, true>(smem)) != FFT_OK) return rc;
-    if ((rc = set_attr_one<MODE, FFT_DT_NAIVE, false>(smem)) != FFT_OK) return rc;
-    if ((rc = set_attr_one<MODE, FFT_DT_NAIVE, true>(smem)) != FFT_OK) return rc;
-    return set_attr_one<MODE, FFT_DT_FP64, false>(smem);
+    if ((rc = set_attr_dt<MODE, FFT_DT_STABLE>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_dt<MODE, FFT_DT_NAIVE>(smem)) != FFT_OK) return rc;
+    return set_attr_one<MODE, FFT_DT_FP64, false, false>(smem);
 }
 
 // Raise the dynamic shared-memory limit of every kernel instantiation once per geometry
@@ -407,7 +481,7 @@ int apply_occupancy(fft_geom g) {
     int per_sm = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<MODE_JT, FFT_DT_STABLE, false>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<MODE_JT, FFT_DT_STABLE, false, false>,
                                                   APPLY_THREADS, apply_smem(g));
     if (per_sm < 1) per_sm = 1;
     if (sms < 1) sms = 1;
@@ -420,14 +494,25 @@ static fft_status launch_mode(fft_geom g, const ApplyParams& P, cudaStream_t st)
     const int ctas = g->apply_ctas;
     FFT_CUDA(cudaMemsetAsync(g->counter, 0, sizeof(int32_t), st));
     if (g->n_items == 0) return FFT_OK;
-#define FFT_LAUNCH(DTV, GV) apply_kernel<MODE, DTV, GV><<<ctas, APPLY_THREADS, smem, st>>>(P)
+#define FFT_LAUNCH(DTV, GV, SV) apply_kernel<MODE, DTV, GV, SV><<<ctas, APPLY_THREADS, smem, st>>>(P)
+#define FFT_LAUNCH_GS(DTV)                                          \
+    do {                                                            \
+        if (g->guard) {                                             \
+            if (g->sharp) FFT_LAUNCH(DTV, true, true);              \
+            else FFT_LAUNCH(DTV, true, false);                      \
+        } else {                                                    \
+            if (g->sharp) FFT_LAUNCH(DTV, false, true);             \
+            else FFT_LAUNCH(DTV, false, false);                     \
+        }                                                           \
+    } while (0)
     if (g->dt_mode == FFT_DT_STABLE) {
-        if (g->guard) FFT_LAUNCH(FFT_DT_STABLE, true); else FFT_LAUNCH(FFT_DT_STABLE, false);
+        FFT_LAUNCH_GS(FFT_DT_STABLE);
     } else if (g->dt_mode == FFT_DT_NAIVE) {
-        if (g->guard) FFT_LAUNCH(FFT_DT_NAIVE, true); else FFT_LAUNCH(FFT_DT_NAIVE, false);
+        FFT_LAUNCH_GS(FFT_DT_NAIVE);
     } else {
-        FFT_LAUNCH(FFT_DT_FP64, false);
+        FFT_LAUNCH(FFT_DT_FP64, false, false);
     }
+#undef FFT_LAUNCH_GS
 #undef FFT_LAUNCH
     FFT_CUDA(cudaGetLastError());
     return FFT_OK;

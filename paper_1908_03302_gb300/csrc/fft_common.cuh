@@ -59,7 +59,14 @@ struct BandConst {
     float h;          // voxel spacing in band units
     float org[3];     // grid origin in band units
     double U;         // band unit length in metres (c0 * dt_max)
+    int32_t sharp;    // Phi just below the cut-off is not negligible: decide the cut in FP64
+    int32_t pad;
 };
+
+// Half-width (in units of the band's maximum detour) of the band around the cut-off inside
+// which a sharp band re-decides "dt < dt_max" in FP64. The FP32 detour near the cut-off is
+// good to ~5e-7 (FP64-derived entry bases, approximate rsqrt / rcp), so 2e-6 keeps a 4x margin.
+constexpr float CUT_BAND = 2e-6f;
 
 // Work item: rows [e0, e1) of tile `tile`'s entry list; J^T writes to slot `slot` of the
 // partial buffer when the tile has several items, else (slot < 0) straight to g.
@@ -90,6 +97,7 @@ struct fft_geom_s {
     int32_t n_tab;
     int32_t dt_mode;
     bool guard;                          // a (virtual) voxel centre coincides with a transducer
+    bool sharp = false;                  // some band's Phi does not vanish at its cut-off
     fftgb::BandConst band[fftgb::MAX_BANDS];
     double dt_max[fftgb::MAX_BANDS];
     // device arrays
@@ -103,7 +111,8 @@ struct fft_geom_s {
     int64_t E = 0;                       // entries
     int64_t* tile_off = nullptr;         // [n_tiles + 1]
     int32_t* tile_rows = nullptr;        // [E]
-    float4* ebase = nullptr;             // [E] (p, c1, c2, c3) of the tile origin in the row's pair frame
+    float4* ebase = nullptr;             // [E] (p + hl, p - hl, c1, c2) of the tile origin in the row's pair frame
+    float* ebase3 = nullptr;             // [E] c3 of the tile origin
     int64_t* row_off = nullptr;          // [M + 1]
     int64_t* row_ent = nullptr;          // [E] tile-major entry ids of each row, ascending
     fftgb::Item* items = nullptr;        // [n_items]

@@ -61,7 +61,8 @@ __device__ __forceinline__ bool box_may_touch(float dx, float dy, float dz, floa
 // transducers normal to the pair axis); then E = 0 and the absolute values drop out.
 // The caller passes ps = p + hl and pr = p - hl (the axial offsets from the emitter and the
 // receiver) directly, so that they can be stepped along a run of voxels.
-template <int DT, bool GUARD, bool INNER = false>
+// RAW: return R / U unsaturated (the caller clamps), so that values just above 1 stay visible.
+template <int DT, bool GUARD, bool INNER = false, bool RAW = false>
 __device__ __forceinline__ float detour_v(float ps, float pr, float q2, float hl, float& is, float& ir) {
     float ss = fmaf(ps, ps, q2), rr = fmaf(pr, pr, q2);
     if (GUARD) {
@@ -71,19 +72,48 @@ __device__ __forceinline__ float detour_v(float ps, float pr, float q2, float hl
     is = rsqrt_approx(ss);
     ir = rsqrt_approx(rr);
     if (DT == FFT_DT_NAIVE) {
-        return __saturatef(fmaf(ss, is, fmaf(rr, ir, -2.0f * hl)));
+        const float v = fmaf(ss, is, fmaf(rr, ir, -2.0f * hl));
+        return RAW ? v : __saturatef(v);
     } else if (INNER) {
         float A = fmaf(ss, is, ps), B = fmaf(rr, ir, -pr);
         float N = q2 * (A + B);
-        return __saturatef(N * rcp_approx(A * B));
+        const float v = N * rcp_approx(A * B);
+        return RAW ? v : __saturatef(v);
     } else {
         float aps = fabsf(ps), apr = fabsf(pr);
         float A = fmaf(ss, is, aps), B = fmaf(rr, ir, apr);   // R_xs + |ps|, R_xr + |pr|
         float N = q2 * (A + B);
         float rP = rcp_approx(A * B);
         float E = (aps - ps) + (apr + pr);
-        return __saturatef(fmaf(N, rP, E));
+        const float v = fmaf(N, rP, E);
+        return RAW ? v : __saturatef(v);
     }
+}
+
+// In-support test dt < dt_max for voxel (ix, iy, iz) and a row given by its transducer
+// positions, evaluated in FP64 with the cancellation-free detour (same arithmetic as the FP64
+// oracle). Used only for the rare voxels whose FP32 detour lies within CUT_BAND of the cut-off
+// of a band whose Phi does not vanish there, so that the in/out decision is taken in FP64.
+static __device__ __forceinline__ bool in_support64(const RowRec64& r, double ox, double oy, double oz, double h, int ix,
+                                          int iy, int iz, double U) {
+    double x = ox + ix * h, y = oy + iy * h, z = oz + iz * h;
+    double ex = r.xr[0] - r.xs[0], ey = r.xr[1] - r.xs[1], ez = r.xr[2] - r.xs[2];
+    double L = sqrt(ex * ex + ey * ey + ez * ez);
+    ex /= L; ey /= L; ez /= L;
+    double dx = x - 0.5 * (r.xs[0] + r.xr[0]), dy = y - 0.5 * (r.xs[1] + r.xr[1]), dz = z - 0.5 * (r.xs[2] + r.xr[2]);
+    double p = dx * ex + dy * ey + dz * ez;
+    double c1 = dy * ez - dz * ey, c2 = dz * ex - dx * ez, c3 = dx * ey - dy * ex;
+    double q2 = c1 * c1 + c2 * c2 + c3 * c3;
+    double hl = 0.5 * L, ps = p + hl, pr = p - hl;
+    double Rs = sqrt(ps * ps + q2), Rr = sqrt(pr * pr + q2);
+    double A = Rs + fabs(ps), B = Rr + fabs(pr);
+    double R = (q2 > 0.0 ? q2 * (A + B) / (A * B) : 0.0) + ((fabs(ps) - ps) + (fabs(pr) + pr));
+    return R < U;
+}
+
+// Applies the FP64 decision to an FP32 normalised detour v near 1.
+__device__ __forceinline__ float settle_cut(float v, bool in) {
+    return in ? fminf(v, 0.99999994f) : 1.0f;
 }
 
 // Table lookup with linear interpolation: Phi(v) for v in [0, 1], tb the shared-memory byte

@@ -91,7 +91,7 @@ __global__ void entry_base_kernel(const int64_t* __restrict__ off, const int32_t
                                   const double* __restrict__ tx, const int32_t* __restrict__ pairs,
                                   const int32_t* __restrict__ row_band, const BandConst* __restrict__ bc,
                                   double ox, double oy, double oz, double h, int tiles_x, int tiles_y,
-                                  float4* __restrict__ ebase) {
+                                  float4* __restrict__ ebase, float* __restrict__ ebase3) {
     const int T = blockIdx.x;
     const int tx_ = T % tiles_x, ty_ = (T / tiles_x) % tiles_y, tz_ = T / (tiles_x * tiles_y);
     const double xT = ox + (double)(TILE_X * tx_) * h;
@@ -110,8 +110,12 @@ __global__ void entry_base_kernel(const int64_t* __restrict__ off, const int32_t
         const double dx = (xT - 0.5 * (xs[0] + xr[0])) / U;
         const double dy = (yT - 0.5 * (xs[1] + xr[1])) / U;
         const double dz = (zT - 0.5 * (xs[2] + xr[2])) / U;
-        ebase[e] = make_float4((float)(dx * ax + dy * ay + dz * az), (float)(dy * az - dz * ay),
-                               (float)(dz * ax - dx * az), (float)(dx * ay - dy * ax));
+        const double pp = dx * ax + dy * ay + dz * az, hl = 0.5 * L / U;
+        // p + hl and p - hl are the axial offsets from the emitter and the receiver; forming
+        // them here keeps them exact when small (voxels near a transducer)
+        ebase[e] = make_float4((float)(pp + hl), (float)(pp - hl), (float)(dy * az - dz * ay),
+                               (float)(dz * ax - dx * az));
+        ebase3[e] = (float)(dx * ay - dy * ax);
     }
 }
 
@@ -173,7 +177,7 @@ fft_status dmalloc(fft_geom g, T** p, size_t count) {
 
 void free_geom(fft_geom g) {
     if (!g) return;
-    void* ptrs[] = {g->d_band, g->rec, g->rec64, g->row_band, g->tab, g->tile_off, g->tile_rows, g->ebase,
+    void* ptrs[] = {g->d_band, g->rec, g->rec64, g->row_band, g->tab, g->tile_off, g->tile_rows, g->ebase, g->ebase3,
                     g->row_off, g->row_ent, g->items, g->tile_slot0, g->tile_nslot, g->jpart,
                     g->gpart, g->counter, g->cg_r, g->cg_q, g->cg_s, g->cg_p, g->cg_d, g->cg_m,
                     g->cg_scal, g->cg_dots, g->cg_status, g->cg_hist};
@@ -273,8 +277,24 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
         hb[b].U = U;
         hb[b].h = (float)(grid->h / U);
         for (int a = 0; a < 3; ++a) hb[b].org[a] = (float)(grid->origin[a] / U);
+        // Is the table's last interior sample (just below the cut-off) non-negligible?
+        std::vector<double> phi(tables[b]->n);
+        cudaError_t ce = cudaMemcpy(phi.data(), tables[b]->d_phi, sizeof(double) * phi.size(), cudaMemcpyDeviceToHost);
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(ce, "fft_geom_create: table copy");
+            free_geom(g);
+            return rc;
+        }
+        double mx = 0.0;
+        for (double v : phi) mx = fmax(mx, fabs(v));
+        hb[b].sharp = (fabs(phi[phi.size() - 1]) > 1e-7 * mx) ? 1 : 0;
+        hb[b].pad = 0;
         g->band[b] = hb[b];
     }
+    bool any_sharp = false;
+    for (int b = 0; b < n_tables; ++b) any_sharp = any_sharp || hb[b].sharp;
+    g->sharp = any_sharp && dt_mode != FFT_DT_FP64;
+    const bool need64 = (dt_mode == FFT_DT_FP64) || any_sharp;
     GEOM_TRY(dmalloc(g, &g->d_band, n_tables));
     GEOM_CUDA(cudaMemcpy(g->d_band, hb.data(), sizeof(BandConst) * n_tables, cudaMemcpyHostToDevice));
 
@@ -289,7 +309,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     // ---- row records
     {
         std::vector<RowRec> rec(n_rows);
-        std::vector<RowRec64> rec64(dt_mode == FFT_DT_FP64 ? n_rows : 0);
+        std::vector<RowRec64> rec64(need64 ? n_rows : 0);
         std::vector<int32_t> rb(n_rows);
         const double h3 = grid->h * grid->h * grid->h;
         for (int64_t p = 0; p < n_rows; ++p) {
@@ -311,7 +331,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
             // K0 dV = -L h^3 / (2 pi c0^3 R_xs R_xr) Phi = C Phi / (Rs_band Rr_band)
             double C = -L * h3 / (2.0 * M_PI * c0 * c0 * c0 * U * U);
             R.b = make_float4((float)(ax / L), (float)(ay / L), (float)(az / L), (float)C);
-            if (dt_mode == FFT_DT_FP64) {
+            if (need64) {
                 for (int a = 0; a < 3; ++a) {
                     rec64[p].xs[a] = xs[a];
                     rec64[p].xr[a] = xr[a];
@@ -322,7 +342,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
         GEOM_TRY(dmalloc(g, &g->row_band, n_rows));
         GEOM_CUDA(cudaMemcpy(g->rec, rec.data(), sizeof(RowRec) * n_rows, cudaMemcpyHostToDevice));
         GEOM_CUDA(cudaMemcpy(g->row_band, rb.data(), sizeof(int32_t) * n_rows, cudaMemcpyHostToDevice));
-        if (dt_mode == FFT_DT_FP64) {
+        if (need64) {
             GEOM_TRY(dmalloc(g, &g->rec64, n_rows));
             GEOM_CUDA(cudaMemcpy(g->rec64, rec64.data(), sizeof(RowRec64) * n_rows, cudaMemcpyHostToDevice));
         }
@@ -380,6 +400,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
 
     // ---- FP64 pair-frame bases of the entries
     GEOM_TRY(dmalloc(g, &g->ebase, g->E));
+    GEOM_TRY(dmalloc(g, &g->ebase3, g->E));
     if (g->E > 0) {
         double* d_tx = nullptr;
         int32_t* d_pairs = nullptr;
@@ -391,7 +412,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
             entry_base_kernel<<<(unsigned)g->n_tiles, 256>>>(g->tile_off, g->tile_rows, d_tx, d_pairs, g->row_band,
                                                              g->d_band, grid->origin[0], grid->origin[1],
                                                              grid->origin[2], grid->h, g->tiles[0], g->tiles[1],
-                                                             g->ebase);
+                                                             g->ebase, g->ebase3);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaDeviceSynchronize();

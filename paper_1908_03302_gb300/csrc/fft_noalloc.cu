@@ -57,7 +57,8 @@ template <int DT>
 __global__ void noalloc_column_kernel(const RowRec* __restrict__ rec, const int32_t* __restrict__ row_band,
                                       const BandConst* __restrict__ bc, const float2* __restrict__ tab, int n_tab,
                                       const int32_t* __restrict__ rows, int n, int64_t M, int nx, int ny,
-                                      int64_t v, float* __restrict__ D, unsigned int* __restrict__ err) {
+                                      int64_t v, const RowRec64* __restrict__ rec64, double3 org64, double h64,
+                                      float* __restrict__ D, unsigned int* __restrict__ err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int p = rows[i];
@@ -77,7 +78,11 @@ __global__ void noalloc_column_kernel(const RowRec* __restrict__ rec, const int3
     const float c1 = fmaf(dy, ez, -dz * ey), c2 = fmaf(dz, ex, -dx * ez), c3 = fmaf(dx, ey, -dy * ex);
     const float q2 = fmaf(c1, c1, fmaf(c2, c2, c3 * c3));
     float is, ir;
-    const float vv = detour_v<DT, true>(pp + r.a.w, pp - r.a.w, q2, r.a.w, is, ir);
+    float vv = detour_v<DT == FFT_DT_NAIVE ? FFT_DT_NAIVE : FFT_DT_STABLE, true, false, true>(pp + r.a.w, pp - r.a.w,
+                                                                                            q2, r.a.w, is, ir);
+    if (c.sharp && fabsf(vv - 1.0f) < CUT_BAND)   // decide the cut of a sharp band in FP64
+        vv = settle_cut(__saturatef(vv), in_support64(rec64[p], org64.x, org64.y, org64.z, h64, ix, iy, iz, c.U));
+    vv = __saturatef(vv);
     const float nm1 = (float)(n_tab - 1);
     const float u = vv * nm1;
     int k = (int)floorf(u);
@@ -117,11 +122,13 @@ extern "C" fft_status fft_psf_noalloc(fft_geom g, int64_t spike_vox, const int32
         if (g->dt_mode == FFT_DT_NAIVE)
             noalloc_column_kernel<FFT_DT_NAIVE><<<blocks, 256, 0, st>>>(
                 g->rec, g->row_band, g->d_band, g->tab, g->n_tab, rows_dev, n_rows, g->M, g->grid.nx, g->grid.ny,
-                spike_vox, D, err);
+                spike_vox, g->rec64, make_double3(g->grid.origin[0], g->grid.origin[1], g->grid.origin[2]), g->grid.h,
+                D, err);
         else
             noalloc_column_kernel<FFT_DT_STABLE><<<blocks, 256, 0, st>>>(
                 g->rec, g->row_band, g->d_band, g->tab, g->n_tab, rows_dev, n_rows, g->M, g->grid.nx, g->grid.ny,
-                spike_vox, D, err);
+                spike_vox, g->rec64, make_double3(g->grid.origin[0], g->grid.origin[1], g->grid.origin[2]), g->grid.h,
+                D, err);
         FFT_CUDA(cudaGetLastError());
     }
     if ((rc = launch_JT(g, D, out_dev, st)) != FFT_OK) return rc;
