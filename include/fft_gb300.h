@@ -198,6 +198,16 @@ fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
 fft_status fft_psf_noalloc(fft_geom g, int64_t spike_vox, const int32_t* rows_dev, int32_t n_rows,
                            float* out_dev, void* stream);
 
+/*
+ * fft_tc_selftest - diagnostic for the tensor-core (tcgen05) path: computes one 128 x n x k
+ * BF16 product with FP32 accumulation in tensor memory on the current device, from
+ * integer-valued operands whose product is exact, and returns the largest absolute difference
+ * from the exact result in *max_abs_err (0 when operand layout and descriptors are right).
+ *   n in {32, 64, 128, 256}; k a multiple of 16 in [16, 256]. Synchronous.
+ * Returns FFT_ERR_TIMEOUT if the bounded wait for the tensor cores gave up.
+ */
+fft_status fft_tc_selftest(int32_t n, int32_t k, double* max_abs_err);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* fft_last_error(void);
 

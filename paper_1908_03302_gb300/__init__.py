@@ -240,6 +240,13 @@ def fft_psf_batch(geom: Geometry, spikes, subsets, mode=0, out=None, stream=None
     return geom.psf_batch(spikes, subsets, mode, out, stream)
 
 
+def tc_selftest(n: int = 128, k: int = 64) -> float:
+    """Largest absolute error of a 128 x n x k BF16 tensor-core product against the exact one."""
+    err = ctypes.c_double()
+    check(_lib.load().fft_tc_selftest(int(n), int(k), ctypes.byref(err)))
+    return err.value
+
+
 # --------------------------------------------------------------------------- autograd
 
 def _make_jfunction():
