@@ -116,6 +116,13 @@ __device__ __forceinline__ float settle_cut(float v, bool in) {
     return in ? fminf(v, 0.99999994f) : 1.0f;
 }
 
+// One entry J[p, v] / C_p-free part times C_p, evaluated directly for voxel (ix, iy, iz) in FP32
+// (pair frame from the row record; cancellation-free detour; FP64 cut decision for sharp bands
+// when rec64 is given). Table lookup from global memory.
+__device__ __forceinline__ float jentry_f32(const RowRec& r, const BandConst& c, const float2* __restrict__ tab,
+                                            int n_tab, const RowRec64* rec64, int p, double ox, double oy,
+                                            double oz, double h64, int ix, int iy, int iz, bool naive);
+
 // Table lookup with linear interpolation: Phi(v) for v in [0, 1], tb the shared-memory byte
 // address of the band table minus (MAGIC bits << 3); nm1 = n_tab - 1. floor(v nm1) comes
 // from a round-down add of MAGIC, whose bit pattern then indexes the table directly.
@@ -126,4 +133,31 @@ __device__ __forceinline__ float phi_lookup(float v, uint32_t tb, float nm1) {
     return fmaf(fr, T.y, T.x);
 }
 
+}  // namespace fftgb
+
+namespace fftgb {
+__device__ __forceinline__ float jentry_f32(const RowRec& r, const BandConst& c, const float2* __restrict__ tab,
+                                            int n_tab, const RowRec64* rec64, int p, double ox, double oy,
+                                            double oz, double h64, int ix, int iy, int iz, bool naive) {
+    const float dx = fmaf((float)ix, c.h, c.org[0]) - r.a.x;
+    const float dy = fmaf((float)iy, c.h, c.org[1]) - r.a.y;
+    const float dz = fmaf((float)iz, c.h, c.org[2]) - r.a.z;
+    const float ex = r.b.x, ey = r.b.y, ez = r.b.z;
+    const float pp = fmaf(dx, ex, fmaf(dy, ey, dz * ez));
+    const float c1 = fmaf(dy, ez, -dz * ey), c2 = fmaf(dz, ex, -dx * ez), c3 = fmaf(dx, ey, -dy * ex);
+    const float q2 = fmaf(c1, c1, fmaf(c2, c2, c3 * c3));
+    float is, ir;
+    float vv = naive ? detour_v<FFT_DT_NAIVE, true, false, true>(pp + r.a.w, pp - r.a.w, q2, r.a.w, is, ir)
+                     : detour_v<FFT_DT_STABLE, true, false, true>(pp + r.a.w, pp - r.a.w, q2, r.a.w, is, ir);
+    if (c.sharp && rec64 && fabsf(vv - 1.0f) < CUT_BAND)
+        vv = settle_cut(__saturatef(vv), in_support64(rec64[p], ox, oy, oz, h64, ix, iy, iz, c.U));
+    vv = __saturatef(vv);
+    const float nm1 = (float)(n_tab - 1);
+    const float u = vv * nm1;
+    int k = (int)floorf(u);
+    if (k > n_tab - 1) k = n_tab - 1;
+    if (k < 0) k = 0;
+    const float2 T = tab[k];
+    return fmaf(u - (float)k, T.y, T.x) * (is * ir) * r.b.w;
+}
 }  // namespace fftgb

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "fft_common.cuh"
@@ -55,18 +56,171 @@ __global__ void column_kernel(const RowRec* __restrict__ rec, const int32_t* __r
     D[p] = phi * (is * ir) * r.b.w;
 }
 
+// mask[rows[i]] |= 1 << s: row membership of subset s.
+__global__ void subset_mask_kernel(const int32_t* __restrict__ rows, int n, int s, uint32_t* __restrict__ mask) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicOr(&mask[rows[i]], 1u << s);
+}
+
+struct DParams {
+    const RowRec* rec;
+    const int32_t* row_band;
+    const BandConst* bc;
+    const float2* tab;
+    int n_tab;
+    const RowRec64* rec64;
+    double ox, oy, oz, h;
+    int nx, ny;
+    const int64_t* spikes;    // spikes of this block
+    int n_k;                  // spikes in the block
+    const uint32_t* mask;
+    int64_t M;
+    bool naive;
+};
+
+// Sparse rows of D for a block of spikes: entry (j = s * n_k + k, J[p, spike_k]) for every
+// subset s holding row p and every spike k with a non-zero entry. COUNT pass writes cnt[p],
+// FILL pass writes at off[p].
+template <bool FILL>
+__global__ void dsparse_kernel(const DParams D, int32_t* __restrict__ cnt, const int64_t* __restrict__ off,
+                               uint16_t* __restrict__ idx, float* __restrict__ val) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= D.M) return;
+    const uint32_t mk = D.mask[p];
+    if (mk == 0) {
+        if (!FILL) cnt[p] = 0;
+        return;
+    }
+    const RowRec r = D.rec[p];
+    const int b = D.row_band[p];
+    const BandConst c = D.bc[b];
+    int n = 0;
+    int64_t o = FILL ? off[p] : 0;
+    for (int k = 0; k < D.n_k; ++k) {
+        const int64_t v = D.spikes[k];
+        const int ix = (int)(v % D.nx), iy = (int)((v / D.nx) % D.ny), iz = (int)(v / ((int64_t)D.nx * D.ny));
+        const float jv = jentry_f32(r, c, D.tab + (int64_t)b * D.n_tab, D.n_tab, D.rec64, (int)p, D.ox, D.oy, D.oz,
+                                    D.h, ix, iy, iz, D.naive);
+        if (jv == 0.0f) continue;
+        for (uint32_t m = mk; m; m &= m - 1) {
+            const int s = __ffs(m) - 1;
+            if (FILL) {
+                idx[o + n] = (uint16_t)(s * D.n_k + k);
+                val[o + n] = jv;
+            }
+            ++n;
+        }
+    }
+    if (!FILL) cnt[p] = n;
+}
+
 }  // namespace
 
 }  // namespace fftgb
 
 using namespace fftgb;
 
+namespace {
+
+// Tensor-core path: spikes in blocks so that (subsets x spikes) <= 512 columns per launch.
+fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, const int32_t* subset_off,
+                       int32_t n_subsets, const int32_t* d_rows, float* out_dev, cudaStream_t st) {
+    const int k_blk = std::max(1, 512 / n_subsets);
+    uint32_t* d_mask = nullptr;
+    int32_t* d_cnt = nullptr;
+    int64_t* d_off = nullptr;
+    int64_t* d_spk = nullptr;
+    int32_t* d_map = nullptr;
+    uint16_t* d_idx = nullptr;
+    float* d_val = nullptr;
+    fft_status rc = FFT_OK;
+    cudaError_t e = cudaMalloc(&d_mask, sizeof(uint32_t) * g->M);
+    if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int32_t) * g->M);
+    if (e == cudaSuccess) e = cudaMalloc(&d_off, sizeof(int64_t) * (g->M + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d_spk, sizeof(int64_t) * n_spike);
+    if (e == cudaSuccess) e = cudaMalloc(&d_map, sizeof(int32_t) * 512);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_mask, 0, sizeof(uint32_t) * g->M, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_spk, spike_vox, sizeof(int64_t) * n_spike, cudaMemcpyHostToDevice, st);
+    for (int s = 0; s < n_subsets && e == cudaSuccess; ++s) {
+        const int n = subset_off[s + 1] - subset_off[s];
+        if (n > 0) {
+            subset_mask_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(d_rows + subset_off[s], n, s, d_mask);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(out_dev, 0, sizeof(float) * (size_t)n_subsets * n_spike * g->V, st);
+    std::vector<int32_t> cnt(g->M);
+    std::vector<int64_t> off(g->M + 1);
+    std::vector<int32_t> cmap;
+    for (int k0 = 0; k0 < n_spike && e == cudaSuccess && rc == FFT_OK; k0 += k_blk) {
+        const int nk = std::min(k_blk, n_spike - k0);
+        DParams D;
+        D.rec = g->rec;
+        D.row_band = g->row_band;
+        D.bc = g->d_band;
+        D.tab = g->tab;
+        D.n_tab = g->n_tab;
+        D.rec64 = g->rec64;
+        D.ox = g->grid.origin[0];
+        D.oy = g->grid.origin[1];
+        D.oz = g->grid.origin[2];
+        D.h = g->grid.h;
+        D.nx = g->grid.nx;
+        D.ny = g->grid.ny;
+        D.spikes = d_spk + k0;
+        D.n_k = nk;
+        D.mask = d_mask;
+        D.M = g->M;
+        D.naive = (g->dt_mode == FFT_DT_NAIVE);
+        const unsigned blocks = (unsigned)ceil_div(g->M, 128);
+        dsparse_kernel<false><<<blocks, 128, 0, st>>>(D, d_cnt, nullptr, nullptr, nullptr);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * g->M, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        off[0] = 0;
+        for (int64_t p = 0; p < g->M; ++p) off[p + 1] = off[p] + cnt[p];
+        const int64_t nnz = off[g->M];
+        cudaFree(d_idx);
+        cudaFree(d_val);
+        d_idx = nullptr;
+        d_val = nullptr;
+        e = cudaMalloc(&d_idx, sizeof(uint16_t) * (nnz > 0 ? nnz : 1));
+        if (e == cudaSuccess) e = cudaMalloc(&d_val, sizeof(float) * (nnz > 0 ? nnz : 1));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * (g->M + 1), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && nnz > 0) {
+            dsparse_kernel<true><<<blocks, 128, 0, st>>>(D, nullptr, d_off, d_idx, d_val);
+            e = cudaGetLastError();
+        }
+        // column (s * nk + k) of this block is output (s * n_spike + k0 + k)
+        cmap.assign((size_t)n_subsets * nk, 0);
+        for (int s = 0; s < n_subsets; ++s)
+            for (int k = 0; k < nk; ++k) cmap[(size_t)s * nk + k] = s * n_spike + k0 + k;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_map, cmap.data(), sizeof(int32_t) * cmap.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && nnz > 0) rc = launch_psf_tc(g, d_off, d_idx, d_val, n_subsets * nk, d_map, out_dev, st);
+    }
+    cudaFree(d_mask);
+    cudaFree(d_cnt);
+    cudaFree(d_off);
+    cudaFree(d_spk);
+    cudaFree(d_map);
+    cudaFree(d_idx);
+    cudaFree(d_val);
+    if (rc != FFT_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "fft_psf_batch (tensor cores)");
+    return FFT_OK;
+}
+
+}  // namespace
+
 extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
                                     const int32_t* subset_off, int32_t n_subsets, const int32_t* subset_rows,
                                     int32_t mode, float* out_dev, void* stream) {
     FFT_ARG(g && spike_vox && subset_off && out_dev, "fft_psf_batch: null argument");
     FFT_ARG(n_spike >= 1 && n_subsets >= 1, "fft_psf_batch: need at least one spike and one subset");
-    FFT_ARG(mode == 0, "fft_psf_batch: mode must be 0 (FP32)");
+    FFT_ARG(mode == 0 || mode == 1, "fft_psf_batch: mode must be 0 (FP32) or 1 (BF16 tensor cores)");
+    FFT_ARG(mode == 0 || n_subsets <= 32, "fft_psf_batch: the tensor-core path takes at most 32 subsets");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
     for (int k = 0; k < n_spike; ++k)
@@ -78,33 +232,51 @@ extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_
     FFT_ARG(n_idx == 0 || subset_rows, "fft_psf_batch: null subset_rows");
     for (int32_t i = 0; i < n_idx; ++i)
         FFT_ARG(subset_rows[i] >= 0 && subset_rows[i] < g->M, "fft_psf_batch: subset row out of range");
+    if (mode == 1) {
+        std::vector<uint8_t> seen;
+        for (int s = 0; s < n_subsets; ++s) {
+            seen.assign(g->M, 0);
+            for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) {
+                FFT_ARG(!seen[subset_rows[i]], "fft_psf_batch: a subset lists a row twice");
+                seen[subset_rows[i]] = 1;
+            }
+        }
+    }
 
     cudaStream_t st = (cudaStream_t)stream;
     int32_t* d_rows = nullptr;
-    float* D = nullptr;
     FFT_CUDA(cudaMalloc(&d_rows, sizeof(int32_t) * (n_idx > 0 ? n_idx : 1)));
-    cudaError_t e = cudaMalloc(&D, sizeof(float) * g->M);
+    cudaError_t e = cudaSuccess;
+    if (n_idx > 0) e = cudaMemcpyAsync(d_rows, subset_rows, sizeof(int32_t) * n_idx, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && mode == 1) {
+        rc = psf_tc_path(g, spike_vox, n_spike, subset_off, n_subsets, d_rows, out_dev, st);
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(d_rows);
+        if (rc != FFT_OK) return rc;
+        if (e2 != cudaSuccess) return cuda_fail(e2, "fft_psf_batch sync");
+        return FFT_OK;
+    }
+    float* D = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&D, sizeof(float) * g->M);
     if (e != cudaSuccess) {
         cudaFree(d_rows);
         return cuda_fail(e, "fft_psf_batch cudaMalloc");
     }
-    if (n_idx > 0) e = cudaMemcpyAsync(d_rows, subset_rows, sizeof(int32_t) * n_idx, cudaMemcpyHostToDevice, st);
     for (int s = 0; s < n_subsets && e == cudaSuccess && rc == FFT_OK; ++s) {
         const int32_t a = subset_off[s], n = subset_off[s + 1] - a;
         for (int k = 0; k < n_spike && e == cudaSuccess && rc == FFT_OK; ++k) {
             e = cudaMemsetAsync(D, 0, sizeof(float) * g->M, st);
             if (e != cudaSuccess) break;
             if (n > 0) {
+                const double3 o64 = make_double3(g->grid.origin[0], g->grid.origin[1], g->grid.origin[2]);
                 if (g->dt_mode == FFT_DT_NAIVE)
                     column_kernel<FFT_DT_NAIVE><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
                         g->rec, g->row_band, g->d_band, g->tab, g->n_tab, d_rows + a, n, g->grid.nx, g->grid.ny,
-                        spike_vox[k], g->rec64, make_double3(g->grid.origin[0], g->grid.origin[1], g->grid.origin[2]),
-                        g->grid.h, D);
+                        spike_vox[k], g->rec64, o64, g->grid.h, D);
                 else
                     column_kernel<FFT_DT_STABLE><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
                         g->rec, g->row_band, g->d_band, g->tab, g->n_tab, d_rows + a, n, g->grid.nx, g->grid.ny,
-                        spike_vox[k], g->rec64, make_double3(g->grid.origin[0], g->grid.origin[1], g->grid.origin[2]),
-                        g->grid.h, D);
+                        spike_vox[k], g->rec64, o64, g->grid.h, D);
                 e = cudaGetLastError();
                 if (e != cudaSuccess) break;
             }

@@ -1,0 +1,467 @@
+// Batched Hessian point-spread functions on the tensor cores (Sec. II-D, Eq. resolution_2):
+//
+//   Y[v, j] = sum_p J[p, v] D[p, j],   D[p, j] = J[p, spike_k] [p in S_s],  j = s * n_spike + k
+//
+// i.e. Y = J^T D with many right-hand sides, which is a dense contraction per voxel block:
+// for an 8 x 4 x 4 sub-brick (128 voxels = the MMA's M) the rows whose support reaches it are
+// the contraction dimension K and the (subset, spike) columns are N.
+//
+// Per CTA (one per SM, 16 warps) and sub-brick:
+//   1. scan the tile's candidate rows, keep those that may reach the sub-brick (tangent-plane
+//      bound of the convex detour), compact them in shared memory;
+//   2. for every chunk of 32 kept rows: warp 0 stages the rows' pair-frame data, all warps
+//      clear the B tile and scatter the rows' sparse D entries into it (BF16), then generate
+//      the A tile J[p, v] (FP32 evaluation as in the J^T kernel, rounded to BF16); one thread
+//      issues tcgen05.mma (M = 128, N = up to 2 x 256, K = 32) accumulating in TMEM and
+//      commits to the buffer's mbarrier; A / B / staging are double-buffered, so generation
+//      of chunk c + 1 overlaps the MMAs of chunk c;
+//   3. after the last chunk, TMEM -> registers -> Y.
+// Every wait is bounded; a time-out sets a status word and the kernel drains and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fft_common.cuh"
+#include "fft_device.cuh"
+#include "fft_tc.cuh"
+
+namespace fftgb {
+
+namespace {
+
+constexpr int TC_WARPS = 16;
+constexpr int TC_THREADS = TC_WARPS * 32;
+constexpr int KC = 32;                 // rows per chunk (MMA K per chunk)
+constexpr int SEG = 1024;              // tile entries scanned per pass
+constexpr int LIST_CAP = SEG + KC;
+constexpr long long WAIT_BUDGET = 4000000000ll;   // cycles (~2 s)
+
+struct PsfTcParams {
+    const RowRec* rec;
+    const int32_t* row_band;
+    const BandConst* bc;
+    const float2* tab;
+    int n_bands, n_tab;
+    const int32_t* tile_rows;
+    const int64_t* tile_off;
+    const float4* ebase;
+    const float* ebase3;
+    const int32_t* units;      // (tile << 4) | sub-brick, heaviest tiles first
+    int n_units;
+    int32_t* counter;
+    int tiles_x, tiles_y;
+    int nx, ny, nz;
+    const int64_t* d_off;      // sparse D rows: [M + 1]
+    const uint16_t* d_idx;     // column j
+    const float* d_val;
+    int n_rhs;                 // columns of D / Y
+    const int32_t* col_map;    // output column of each D column
+    int n_half;                // N of one MMA (multiple of 16, <= 256)
+    int nh;                    // MMAs per K step (1 or 2)
+    int b_rows;                // rows of the B tile (nh * n_half)
+    int tmem_cols;
+    float* out;                // Y as out[j * V + v]
+    int64_t V;
+    int32_t* status;
+};
+
+struct TcShared {
+    unsigned long long mbar[2];
+    uint32_t tmem_slot;
+    int unit;
+    int wcnt[TC_WARPS];
+    int n_list;
+};
+
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!tc::mbar_try_wait(mbar, parity)) {
+        if (clock64() - t0 > WAIT_BUDGET) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_constant__ PsfTcParams P) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ TcShared S;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // ---- shared-memory carve-up: A[2], B[2] (1 KB aligned), table, staging, row list
+    const uint32_t a_bytes = 128u * KC * 2u;
+    const uint32_t b_bytes = (uint32_t)P.b_rows * KC * 2u;
+    unsigned char* sA0 = smem;
+    unsigned char* sB0 = smem + 2 * a_bytes;
+    size_t off = 2 * (size_t)a_bytes + 2 * (size_t)b_bytes;
+    float2* s_tab = reinterpret_cast<float2*>(smem + off);
+    off += ((size_t)P.n_bands * P.n_tab * sizeof(float2) + 15) & ~(size_t)15;
+    float4* s_stg = reinterpret_cast<float4*>(smem + off);          // [2][KC][3]
+    off += 2 * KC * 3 * sizeof(float4);
+    int32_t* s_row = reinterpret_cast<int32_t*>(smem + off);        // [2][KC] row index or -1
+    off += 2 * KC * sizeof(int32_t);
+    int64_t* s_list = reinterpret_cast<int64_t*>(smem + off);       // [LIST_CAP]
+
+    for (int i = tid; i < P.n_bands * P.n_tab; i += TC_THREADS) s_tab[i] = P.tab[i];
+    const uint32_t tab_addr = smem_addr(s_tab);
+    const float nm1 = (float)(P.n_tab - 1);
+    const uint32_t mbar0 = smem_addr(&S.mbar[0]);
+    if (warp == 0) {
+        tc::tmem_alloc(smem_addr(&S.tmem_slot), (uint32_t)P.tmem_cols);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(mbar0, 1);
+        tc::mbar_init(mbar0 + 8, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = S.tmem_slot;
+    const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)P.n_half);
+
+    int chunk = 0;        // chunks issued by this CTA so far (selects buffer and mbarrier phase)
+    bool failed = false;
+    // generation role: row group g (rows 8g .. 8g + 7 of a chunk), voxel (x, y, z) of the sub-brick
+    const int g = warp & 3;
+    const int vx = lane & 7, vy = lane >> 3, vz = warp >> 2;
+    const int m_row = 32 * vz + lane;   // MMA row (TMEM lane) of this voxel
+
+    for (;;) {
+        __syncthreads();   // everyone has read the previous unit index before it is replaced
+        if (tid == 0) S.unit = atomicAdd(P.counter, 1);
+        __syncthreads();
+        const int unit = S.unit;
+        if (unit >= P.n_units || failed) break;
+        const int T = P.units[unit] >> 4, sb = P.units[unit] & 15;
+        const int tx = T % P.tiles_x, ty = (T / P.tiles_x) % P.tiles_y, tz = T / (P.tiles_x * P.tiles_y);
+        // sub-brick origin in the tile (8 x 4 x 4 bricks: 2 along x, 4 along y, 2 along z)
+        const int SX = 8 * (sb & 1), SY = 4 * ((sb >> 1) & 3), SZ = 4 * (sb >> 3);
+        const int X0 = TILE_X * tx + SX, Y0 = TILE_Y * ty + SY, Z0 = TILE_Z * tz + SZ;
+        if (X0 >= P.nx || Y0 >= P.ny || Z0 >= P.nz) continue;   // uniform across the CTA
+        const int64_t e_begin = P.tile_off[T], e_end = P.tile_off[T + 1];
+        // this thread's voxel offset inside the tile (generation)
+        const float Xv = (float)(SX + vx), Yv = (float)(SY + vy), Zv = (float)(SZ + vz);
+        int n_list = 0, head = 0, unit_chunks = 0;
+
+        for (int64_t seg = e_begin; seg < e_end; seg += SEG) {
+            // ---- 1. scan: keep rows that may reach the sub-brick; move the carry to the front
+            if (head > 0) {
+                const int carry = n_list - head;
+                int64_t v = (tid < carry) ? s_list[head + tid] : 0;
+                __syncthreads();
+                if (tid < carry) s_list[tid] = v;
+                n_list = carry;
+                head = 0;
+            }
+            for (int pass = 0; pass < SEG / TC_THREADS; ++pass) {
+                const int64_t e = seg + pass * TC_THREADS + tid;
+                bool keep = false;
+                if (e < e_end) {
+                    const int p = P.tile_rows[e];
+                    if (P.d_off[p + 1] > P.d_off[p]) {   // rows without D entries add nothing
+                    const RowRec r = P.rec[p];
+                    const BandConst bc = P.bc[P.row_band[p]];
+                    const float hb = bc.h;
+                    const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
+                    const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
+                    const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
+                    keep = box_may_touch(cx, cy, cz, r.b.x, r.b.y, r.b.z, r.a.w, 3.5f * hb, 1.5f * hb, 1.5f * hb);
+                    }
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) S.wcnt[warp] = __popc(bal);
+                __syncthreads();
+                int before = 0, total = 0;
+#pragma unroll
+                for (int w = 0; w < TC_WARPS; ++w) {
+                    const int c = S.wcnt[w];
+                    before += (w < warp) ? c : 0;
+                    total += c;
+                }
+                if (keep) s_list[n_list + before + __popc(bal & ((1u << lane) - 1u))] = e;
+                n_list += total;
+                __syncthreads();
+            }
+            const bool last_seg = seg + SEG >= e_end;
+            // ---- 2. chunks of KC kept rows
+            while (n_list - head >= KC || (last_seg && n_list - head > 0)) {
+                const int nrows = min(KC, n_list - head);
+                const int buf = chunk & 1;
+                unsigned char* sA = sA0 + buf * a_bytes;
+                unsigned char* sB = sB0 + buf * b_bytes;
+                float4* stg = s_stg + buf * KC * 3;
+                int32_t* srow = s_row + buf * KC;
+                if (chunk >= 2) {
+                    // the MMAs that last read this buffer must be done before it is rewritten
+                    if (!wait_phase(mbar0 + 8u * buf, (uint32_t)(((chunk >> 1) - 1) & 1))) {
+                        if (tid == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
+                        failed = true;
+                    }
+                }
+                if (__syncthreads_or(failed)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                // stage rows (warp 0) and clear the B tile (everyone)
+                if (warp == 0) {
+                    int p = -1;
+                    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
+                    if (lane < nrows) {
+                        const int64_t e = s_list[head + lane];
+                        p = P.tile_rows[e];
+                        const float4 base = P.ebase[e];
+                        const float base3 = P.ebase3[e];
+                        const RowRec r = P.rec[p];
+                        const int b = P.row_band[p];
+                        const BandConst bc = P.bc[b];
+                        const float hb = bc.h;
+                        const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
+                        // is the whole sub-brick between the transducer planes?
+                        const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
+                        const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
+                        const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
+                        const float pext = 3.5f * hb * fabsf(ex) + 1.5f * hb * (fabsf(ey) + fabsf(ez)) + 1e-3f;
+                        const bool inner = fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl;
+                        const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
+                        s0 = base;
+                        s1 = make_float4(hb * ex, hb * ey, hb * ez, base3);
+                        s2 = make_float4(r.b.w, __uint_as_float(tb), inner ? 1.0f : 0.0f, 0.0f);
+                    }
+                    stg[lane * 3 + 0] = s0;
+                    stg[lane * 3 + 1] = s1;
+                    stg[lane * 3 + 2] = s2;
+                    srow[lane] = p;
+                }
+                {
+                    uint4* b4 = reinterpret_cast<uint4*>(sB);
+                    for (uint32_t i = tid; i < b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
+                }
+                __syncthreads();
+                // scatter the kept rows' sparse D entries into B (column j, row r)
+                {
+                    const int r = tid >> 4, i0 = tid & 15;
+                    const int p = srow[r];
+                    if (p >= 0) {
+                        for (int64_t i = P.d_off[p] + i0; i < P.d_off[p + 1]; i += 16) {
+                            const int j = P.d_idx[i];
+                            *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)j, (uint32_t)r, KC)) =
+                                __float2bfloat16_rn(P.d_val[i]);
+                        }
+                    }
+                }
+                // generate A: this thread's voxel, rows 8 g .. 8 g + 7 of the chunk
+                {
+                    float vals[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int r = 8 * g + q;
+                        const float4 A4 = stg[r * 3 + 0];
+                        const float4 B4 = stg[r * 3 + 1];
+                        const float4 C4 = stg[r * 3 + 2];
+                        float val = 0.0f;
+                        if (r < nrows) {
+                            const float hx = B4.x, hy = B4.y, hz = B4.z;
+                            const float o = fmaf(Xv, hx, fmaf(Yv, hy, Zv * hz));
+                            const float ps = A4.x + o, pr = A4.y + o;
+                            const float c1 = fmaf(Yv, hz, fmaf(-Zv, hy, A4.z));
+                            const float c2 = fmaf(Zv, hx, fmaf(-Xv, hz, A4.w));
+                            const float c3 = fmaf(Xv, hy, fmaf(-Yv, hx, B4.w));
+                            const float q2 = fmaf(c1, c1, fmaf(c2, c2, c3 * c3));
+                            float is, ir, v;
+                            if (C4.z != 0.0f)
+                                v = detour_v<FFT_DT_STABLE, true, true>(ps, pr, q2, 0.0f, is, ir);
+                            else
+                                v = detour_v<FFT_DT_STABLE, true, false>(ps, pr, q2, 0.0f, is, ir);
+                            val = phi_lookup(v, __float_as_uint(C4.y), nm1) * (is * ir) * C4.x;
+                        }
+                        vals[q] = val;
+                    }
+                    uint4 packed = make_uint4(pack_bf16x2(vals[0], vals[1]), pack_bf16x2(vals[2], vals[3]),
+                                              pack_bf16x2(vals[4], vals[5]), pack_bf16x2(vals[6], vals[7]));
+                    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset((uint32_t)m_row, (uint32_t)(8 * g), KC)) = packed;
+                }
+                tc::fence_proxy_async_smem();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (tid == 0) {
+                    const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ++ks) {
+                        const uint64_t ad = tc::smem_desc(a_base + 256u * ks, 128u, 16u * KC);
+                        for (int h = 0; h < P.nh; ++h) {
+                            const uint64_t bd =
+                                tc::smem_desc(b_base + (uint32_t)(h * P.n_half) * (KC * 2u) + 256u * ks, 128u, 16u * KC);
+                            tc::mma_bf16(taddr + (uint32_t)(h * P.n_half), ad, bd, idesc,
+                                         (unit_chunks > 0 || ks > 0) ? 1u : 0u);
+                        }
+                    }
+                    tc::mma_commit(mbar0 + 8u * buf);
+                }
+                ++chunk;
+                ++unit_chunks;
+                head += nrows;
+            }
+            if (failed) break;
+        }
+        if (failed) break;
+        if (unit_chunks == 0) continue;
+        // ---- 3. all MMAs of this unit done -> TMEM -> Y
+        {
+            const int last = chunk - 1;
+            if (!wait_phase(mbar0 + 8u * (last & 1), (uint32_t)((last >> 1) & 1))) {
+                if (tid == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
+                failed = true;
+            }
+        }
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        tc::fence_after_sync();
+        {
+            const int quarter = warp & 3;              // TMEM lanes this warp may access
+            const int mm = 32 * quarter + lane;         // voxel m of the sub-brick
+            const int x = X0 + (mm & 7), y = Y0 + ((mm >> 3) & 3), z = Z0 + (mm >> 5);
+            const bool valid = x < P.nx && y < P.ny && z < P.nz;
+            const int64_t v = ((int64_t)z * P.ny + y) * P.nx + x;
+            const int cols = P.nh * P.n_half;
+            for (int c = 8 * (warp >> 2); c < cols; c += 32) {
+                float vals[8];
+                tc::tmem_ld_x8(taddr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c, vals);
+                if (valid) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (c + i < P.n_rhs) P.out[(int64_t)P.col_map[c + i] * P.V + v] = vals[i];
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    // drain: every issued MMA must be complete before the accumulator is released
+    if (chunk > 0) {
+        const int last = chunk - 1;
+        wait_phase(mbar0 + 8u * (last & 1), (uint32_t)((last >> 1) & 1));
+        if (chunk > 1) wait_phase(mbar0 + 8u * ((last - 1) & 1), (uint32_t)(((last - 1) >> 1) & 1));
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)P.tmem_cols);
+}
+
+}  // namespace
+
+// Y = J^T D on the tensor cores for D given as sparse rows (d_off, d_idx, d_val) with n_rhs
+// columns (1 .. 512); column j of Y goes to out[col_map[j] * V + v]. out must be zeroed by the
+// caller (voxels that no row reaches are not written). Synchronous; returns FFT_ERR_TIMEOUT if
+// a bounded wait gave up.
+fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx, const float* d_val, int n_rhs,
+                         const int32_t* col_map, float* out, cudaStream_t st) {
+    if (n_rhs < 1 || n_rhs > 512) {
+        set_error("psf tensor-core path: 1 .. 512 right-hand sides per launch");
+        return FFT_ERR_ARG;
+    }
+    if (g->E == 0) return FFT_OK;
+    const int nh = n_rhs > 256 ? 2 : 1;
+    const int n_half = (int)ceil_div(ceil_div(n_rhs, nh), 16) * 16;
+    int cols = nh * n_half, tmem_cols = 32;
+    while (tmem_cols < cols) tmem_cols <<= 1;
+
+    // units: the 16 sub-bricks of every tile with candidate rows, heaviest tiles first
+    std::vector<int64_t> toff(g->n_tiles + 1);
+    FFT_CUDA(cudaMemcpy(toff.data(), g->tile_off, sizeof(int64_t) * (g->n_tiles + 1), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> tiles;
+    for (int64_t T = 0; T < g->n_tiles; ++T)
+        if (toff[T + 1] > toff[T]) tiles.push_back((int32_t)T);
+    std::stable_sort(tiles.begin(), tiles.end(),
+                     [&](int32_t a, int32_t b) { return toff[a + 1] - toff[a] > toff[b + 1] - toff[b]; });
+    std::vector<int32_t> units;
+    units.reserve(tiles.size() * 16);
+    for (int32_t T : tiles)
+        for (int s = 0; s < 16; ++s) units.push_back((T << 4) | s);
+    if (units.empty()) return FFT_OK;
+
+    int32_t *d_units = nullptr, *d_ctr = nullptr;
+    FFT_CUDA(cudaMalloc(&d_units, sizeof(int32_t) * units.size()));
+    cudaError_t e = cudaMalloc(&d_ctr, 2 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_units, units.data(), sizeof(int32_t) * units.size(),
+                                              cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(int32_t), st);
+
+    PsfTcParams P;
+    P.rec = g->rec;
+    P.row_band = g->row_band;
+    P.bc = g->d_band;
+    P.tab = g->tab;
+    P.n_bands = g->n_bands;
+    P.n_tab = g->n_tab;
+    P.tile_rows = g->tile_rows;
+    P.tile_off = g->tile_off;
+    P.ebase = g->ebase;
+    P.ebase3 = g->ebase3;
+    P.units = d_units;
+    P.n_units = (int)units.size();
+    P.counter = d_ctr;
+    P.tiles_x = g->tiles[0];
+    P.tiles_y = g->tiles[1];
+    P.nx = g->grid.nx;
+    P.ny = g->grid.ny;
+    P.nz = g->grid.nz;
+    P.d_off = d_off;
+    P.d_idx = d_idx;
+    P.d_val = d_val;
+    P.n_rhs = n_rhs;
+    P.col_map = col_map;
+    P.n_half = n_half;
+    P.nh = nh;
+    P.b_rows = nh * n_half;
+    P.tmem_cols = tmem_cols;
+    P.out = out;
+    P.V = g->V;
+    P.status = d_ctr + 1;
+
+    // at least 120 KB so that only one CTA (which holds TMEM for the whole launch) fits on an SM
+    const size_t smem = std::max<size_t>(
+        120 * 1024, 2 * (size_t)(128 * KC * 2) + 2 * (size_t)P.b_rows * KC * 2 +
+                        (((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15) +
+                        2 * KC * 3 * sizeof(float4) + 2 * KC * sizeof(int32_t) + LIST_CAP * sizeof(int64_t));
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess && smem + sizeof(TcShared) > (size_t)optin) {
+        cudaFree(d_units);
+        cudaFree(d_ctr);
+        set_error("psf tensor-core path: tables and tiles do not fit in shared memory");
+        return FFT_ERR_ARG;
+    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(psf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        psf_tc_kernel<<<sms, TC_THREADS, smem, st>>>(P);
+        e = cudaGetLastError();
+    }
+    int32_t status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_ctr + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_units);
+    cudaFree(d_ctr);
+    if (e != cudaSuccess) return cuda_fail(e, "psf tensor-core path");
+    if (status != 0) {
+        set_error("psf tensor-core path: a bounded wait for the tensor cores timed out");
+        return FFT_ERR_TIMEOUT;
+    }
+    return FFT_OK;
+}
+
+}  // namespace fftgb

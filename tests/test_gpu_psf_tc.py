@@ -1,0 +1,72 @@
+"""Batched Hessian PSFs on the tensor cores (BF16 operands, FP32 accumulation in TMEM)
+against the FP64 oracle (relative L2 <= 1e-2 per PSF) and against the FP32 CUDA-core path,
+including more than 256 right-hand sides (two MMAs per K step) and more than 512 (spike
+blocks)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+from gpu_common import gpu_geometry, oracle_geometry, rel_l2, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def ring_subsets32(M_pairs):
+    local = wl.unordered_pairs(range(32))
+    out = []
+    for st in (4, 2, 1):
+        out.append(np.flatnonzero((local[:, 0] % st == 0) & (local[:, 1] % st == 0)).astype(np.int32))
+    return out
+
+
+@pytest.fixture(scope="module")
+def ring32():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w, og = oracle_geometry("ring32")
+    geo, tabs = gpu_geometry(w)
+    return w, og, geo
+
+
+def test_psf_tc_matches_oracle(ring32):
+    w, og, geo = ring32
+    spikes = wl.random_voxels(w.grid, 6, 8, rho_max=0.035, z_max=0.012)
+    subsets = ring_subsets32(og.M)
+    ref = og.psf(spikes, subsets)
+    tc = to_np(geo.psf_batch(spikes, subsets, mode=1))
+    fp = to_np(geo.psf_batch(spikes, subsets, mode=0))
+    for s in range(len(subsets)):
+        for k in range(len(spikes)):
+            assert rel_l2(fp[s, k], ref[s, k]) <= 1e-5
+            assert rel_l2(tc[s, k], ref[s, k]) <= 1e-2
+
+
+@pytest.mark.parametrize("n_spike", [100, 200])
+def test_psf_tc_many_rhs(ring32, n_spike):
+    # 3 subsets x 100 spikes = 300 columns (two MMAs per K step);
+    # 3 x 200 = 600 columns (spike blocks of 170)
+    w, og, geo = ring32
+    spikes = wl.random_voxels(w.grid, n_spike, 9, rho_max=0.04, z_max=0.014)
+    subsets = ring_subsets32(og.M)
+    tc = to_np(geo.psf_batch(spikes, subsets, mode=1))
+    fp = to_np(geo.psf_batch(spikes, subsets, mode=0))
+    errs = [rel_l2(tc[s, k], fp[s, k]) for s in range(3) for k in range(n_spike)
+            if np.linalg.norm(fp[s, k]) > 0]
+    assert len(errs) > 0 and max(errs) <= 1e-2
+
+
+def test_psf_tc_ragged_tiny(fg_tiny=None):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w, og = oracle_geometry("tiny")
+    geo, _ = gpu_geometry(w)
+    spikes = np.array([200, 611, 950], dtype=np.int64)
+    subsets = [np.arange(0, og.M, 3, dtype=np.int32), np.arange(og.M, dtype=np.int32)]
+    ref = og.psf(spikes, subsets)
+    tc = to_np(geo.psf_batch(spikes, subsets, mode=1))
+    for s in range(2):
+        for k in range(3):
+            assert rel_l2(tc[s, k], ref[s, k]) <= 1e-2
