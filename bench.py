@@ -191,6 +191,96 @@ def run_reference(args, ws, rank):
     return 0
 
 
+# --------------------------------------------------------------------------- PSF batch
+
+def run_psf(args, ws, rank, local):
+    """Batched Hessian PSFs on the slice-by-slice geometry: 128 seeded spikes x 3 nested ring
+    subsets (every 4th / 2nd / every element) = 384 PSFs, BF16 tensor-core path against the
+    FP32 CUDA-core path (per PSF: column J e_k then J^T restricted to the rows it touches)."""
+    import torch
+    import paper_1908_03302_gb300 as fg
+    torch.cuda.set_device(local)
+    w = wl.by_name(args.psf_geometry)
+    tables = [fg.Table(b.f_center_hz, b.f_sigma_hz, b.n_samples, b.dt_max) for b in w.bands]
+    geo = fg.Geometry(w.tx, w.row_pairs(), w.grid, w.c0, tables,
+                      band_of_row=w.band_of_row if len(w.bands) > 1 else None)
+    spikes = wl.random_voxels(w.grid, args.psf_spikes, 8)
+    subsets = wl.ring_subsets(n_slices=16 if w.name == "slices3d" else 1, n_bands=len(w.bands))
+    n_psf = len(spikes) * len(subsets)
+    out_tc = torch.empty(n_psf * geo.V, device="cuda", dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    for _ in range(args.warmup):
+        geo.psf_batch(spikes, subsets, mode=1, out=out_tc)
+    tc_ms = [timed(lambda: geo.psf_batch(spikes, subsets, mode=1, out=out_tc)) for _ in range(args.steps)]
+    if args.psf_tc_only:
+        if rank == 0:
+            print(json.dumps({"psf_tc_ms": tc_ms, "geometry": w.name, "spikes": len(spikes)}), flush=True)
+        return 0
+    # FP32 path on a slice of the spikes (same per-PSF cost), scaled to the whole batch
+    k32 = min(len(spikes), args.psf_fp32_spikes)
+    out_fp = torch.empty(k32 * len(subsets) * geo.V, device="cuda", dtype=torch.float32)
+    fp_ms = timed(lambda: geo.psf_batch(spikes[:k32], subsets, mode=0, out=out_fp))
+    tc = out_tc.view(len(subsets), len(spikes), geo.V)
+    fp = out_fp.view(len(subsets), k32, geo.V)
+    diff = []
+    for sb in range(len(subsets)):
+        for k in range(k32):
+            nrm = float(fp[sb, k].double().norm())
+            if nrm > 0:
+                diff.append(float((tc[sb, k].double() - fp[sb, k].double()).norm()) / nrm)
+    # FP64 oracle on sampled voxels of a few PSFs
+    import oracle
+    og = oracle.Geometry.from_workload(w)
+    rng = np.random.default_rng(12)
+    errs_tc, errs_fp = [], []
+    for k in range(min(2, k32)):
+        vk = int(spikes[k])
+        i, j, z = vk % w.grid.nx, (vk // w.grid.nx) % w.grid.ny, vk // (w.grid.nx * w.grid.ny)
+        near = []
+        for _ in range(256):
+            di, dj, dz = rng.integers(-20, 21, 3)
+            ii, jj, zz = min(max(i + di, 0), w.grid.nx - 1), min(max(j + dj, 0), w.grid.ny - 1), \
+                min(max(z + dz, 0), w.grid.nz - 1)
+            near.append((zz * w.grid.ny + jj) * w.grid.nx + ii)
+        vox = np.unique(np.array(near, dtype=np.int64))
+        for sb in (0, 2):
+            ref = og.psf(np.array([vk]), [subsets[sb]], vox)[0, 0]
+            n = np.linalg.norm(ref)
+            errs_tc.append(float(np.linalg.norm(tc[sb, k][torch.as_tensor(vox, device="cuda")].double().cpu().numpy() - ref) / n))
+            errs_fp.append(float(np.linalg.norm(fp[sb, k][torch.as_tensor(vox, device="cuda")].double().cpu().numpy() - ref) / n))
+    fp_full_ms = fp_ms * len(spikes) / k32
+    tc_avg = statistics.mean(tc_ms)
+    info = geo.info()
+    line = {
+        "metric": "batched Hessian PSFs: ms per batch (BF16 tensor cores vs FP32), PSF rel-L2 vs FP64 oracle",
+        "value": tc_avg, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tc_avg, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 x bf16 -> f32 (tensor cores); f32 generation",
+        "data": "synthetic (seeded slice-by-slice ring geometry, seeded spikes)",
+        "config": {"workload": "psf3d" if w.name == "slices3d" else "psf-" + w.name, "pairs": geo.M, "voxels": geo.V, "spikes": len(spikes),
+                   "subsets": [int(len(sb)) for sb in subsets], "psfs": n_psf,
+                   "support_evals_per_apply": int(info.support_evals)},
+        "fp32_path_ms_per_batch": fp_full_ms, "fp32_path_measured": f"{k32} spikes x 3 subsets, scaled",
+        "speedup_tc_vs_fp32": fp_full_ms / tc_avg,
+        "tc_vs_fp32_rel_l2_max": max(diff) if diff else None,
+        "err_vs_fp64_oracle": {"tc_rel_l2_max": max(errs_tc), "fp32_rel_l2_max": max(errs_fp),
+                               "sample": "2 spikes x subsets {64, 256}, <=256 voxels within 20 of the spike"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -199,7 +289,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ring256", choices=["ring32", "ring256", "slices3d"])
+    ap.add_argument("--workload", default="ring256", choices=["ring32", "ring256", "slices3d", "psf3d"])
+    ap.add_argument("--psf-spikes", type=int, default=128)
+    ap.add_argument("--psf-fp32-spikes", type=int, default=8)
+    ap.add_argument("--psf-geometry", default="slices3d", choices=["slices3d", "ring256"])
+    ap.add_argument("--psf-tc-only", action="store_true", help="time only the tensor-core path (profiling)")
     ap.add_argument("--dt-mode", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=1024)
@@ -212,6 +306,8 @@ def main():
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload == "psf3d":
+        return run_psf(args, ws, rank, local)
 
     import torch
     import paper_1908_03302_gb300 as fg

@@ -156,6 +156,7 @@ fft_status compute_frob2(fft_geom g, double* out);
 fft_status set_apply_attributes(fft_geom g);
 int apply_occupancy(fft_geom g);
 size_t apply_smem(fft_geom g);
+int psf_tc_max_cols(fft_geom g);
 fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx, const float* d_val, int n_rhs,
                          const int32_t* col_map, float* out, cudaStream_t st);
 int64_t ceil_div(int64_t a, int64_t b);

@@ -125,7 +125,12 @@ namespace {
 // Tensor-core path: spikes in blocks so that (subsets x spikes) <= 512 columns per launch.
 fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, const int32_t* subset_off,
                        int32_t n_subsets, const int32_t* d_rows, float* out_dev, cudaStream_t st) {
-    const int k_blk = std::max(1, 512 / n_subsets);
+    const int max_cols = psf_tc_max_cols(g);
+    if (max_cols < n_subsets) {
+        set_error("fft_psf_batch: the tensor-core tiles do not fit in shared memory with these tables");
+        return FFT_ERR_ARG;
+    }
+    const int k_blk = std::max(1, max_cols / n_subsets);
     uint32_t* d_mask = nullptr;
     int32_t* d_cnt = nullptr;
     int64_t* d_off = nullptr;

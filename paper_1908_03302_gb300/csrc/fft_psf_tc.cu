@@ -35,8 +35,9 @@ namespace {
 constexpr int TC_WARPS = 16;
 constexpr int TC_THREADS = TC_WARPS * 32;
 constexpr int KC = 32;                 // rows per chunk (MMA K per chunk)
-constexpr int SEG = 1024;              // tile entries scanned per pass
-constexpr int LIST_CAP = SEG + KC;
+constexpr int NSTAGE = 3;              // A / B buffers in the ring
+constexpr int SEG = TC_THREADS;        // tile entries scanned per pass (one per thread)
+constexpr int LIST_CAP = SEG + KC;     // kept rows waiting for a chunk (staged records)
 constexpr long long WAIT_BUDGET = 4000000000ll;   // cycles (~2 s)
 
 struct PsfTcParams {
@@ -69,7 +70,7 @@ struct PsfTcParams {
 };
 
 struct TcShared {
-    unsigned long long mbar[2];
+    unsigned long long mbar[NSTAGE];
     uint32_t tmem_slot;
     int unit;
     int wcnt[TC_WARPS];
@@ -98,15 +99,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
     const uint32_t a_bytes = 128u * KC * 2u;
     const uint32_t b_bytes = (uint32_t)P.b_rows * KC * 2u;
     unsigned char* sA0 = smem;
-    unsigned char* sB0 = smem + 2 * a_bytes;
-    size_t off = 2 * (size_t)a_bytes + 2 * (size_t)b_bytes;
+    unsigned char* sB0 = smem + NSTAGE * a_bytes;
+    size_t off = NSTAGE * (size_t)a_bytes + NSTAGE * (size_t)b_bytes;
     float2* s_tab = reinterpret_cast<float2*>(smem + off);
     off += ((size_t)P.n_bands * P.n_tab * sizeof(float2) + 15) & ~(size_t)15;
-    float4* s_stg = reinterpret_cast<float4*>(smem + off);          // [2][KC][3]
-    off += 2 * KC * 3 * sizeof(float4);
-    int32_t* s_row = reinterpret_cast<int32_t*>(smem + off);        // [2][KC] row index or -1
-    off += 2 * KC * sizeof(int32_t);
-    int64_t* s_list = reinterpret_cast<int64_t*>(smem + off);       // [LIST_CAP]
+    float4* s_stg = reinterpret_cast<float4*>(smem + off);          // [LIST_CAP][3] staged kept rows
+    off += (size_t)LIST_CAP * 3 * sizeof(float4);
+    int32_t* s_row = reinterpret_cast<int32_t*>(smem + off);        // [LIST_CAP] their row indices
 
     for (int i = tid; i < P.n_bands * P.n_tab; i += TC_THREADS) s_tab[i] = P.tab[i];
     const uint32_t tab_addr = smem_addr(s_tab);
@@ -117,8 +116,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        tc::mbar_init(mbar0, 1);
-        tc::mbar_init(mbar0 + 8, 1);
+        for (int b = 0; b < NSTAGE; ++b) tc::mbar_init(mbar0 + 8u * b, 1);
+    }
+    {   // every B buffer starts cleared; afterwards each is cleared one chunk ahead of its use
+        uint4* b4 = reinterpret_cast<uint4*>(sB0);
+        for (uint32_t i = tid; i < NSTAGE * b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -128,10 +130,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
 
     int chunk = 0;        // chunks issued by this CTA so far (selects buffer and mbarrier phase)
     bool failed = false;
-    // generation role: row group g (rows 8g .. 8g + 7 of a chunk), voxel (x, y, z) of the sub-brick
-    const int g = warp & 3;
-    const int vx = lane & 7, vy = lane >> 3, vz = warp >> 2;
-    const int m_row = 32 * vz + lane;   // MMA row (TMEM lane) of this voxel
+    // Generation role: warp w evaluates rows 2w and 2w + 1 of a chunk; lane l owns the four
+    // consecutive x voxels (4 lx + t, ly, lz), t = 0..3, of the 8 x 4 x 4 sub-brick, with
+    // lx = l & 1, ly = (l >> 1) & 3, lz = l >> 3. Voxel t of lane l is MMA row (TMEM lane)
+    // m = 32 t + l, which spreads a warp's stores over all eight 16-byte slots of a core matrix.
+    const int glx = lane & 1, gly = (lane >> 1) & 3, glz = lane >> 3;
 
     for (;;) {
         __syncthreads();   // everyone has read the previous unit index before it is replaced
@@ -146,33 +149,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         const int X0 = TILE_X * tx + SX, Y0 = TILE_Y * ty + SY, Z0 = TILE_Z * tz + SZ;
         if (X0 >= P.nx || Y0 >= P.ny || Z0 >= P.nz) continue;   // uniform across the CTA
         const int64_t e_begin = P.tile_off[T], e_end = P.tile_off[T + 1];
-        // this thread's voxel offset inside the tile (generation)
-        const float Xv = (float)(SX + vx), Yv = (float)(SY + vy), Zv = (float)(SZ + vz);
+        // this lane's first voxel, relative to the tile origin (generation)
+        const float Xv = (float)(SX + 4 * glx), Yv = (float)(SY + gly), Zv = (float)(SZ + glz);
         int n_list = 0, head = 0, unit_chunks = 0;
 
         for (int64_t seg = e_begin; seg < e_end; seg += SEG) {
-            // ---- 1. scan: keep rows that may reach the sub-brick; move the carry to the front
+            // ---- 1. scan: keep rows that may reach the sub-brick, staged in the row list;
+            //         the rows left over from the previous pass move to the front first
             if (head > 0) {
                 const int carry = n_list - head;
-                int64_t v = (tid < carry) ? s_list[head + tid] : 0;
+                float4 c0, c1, c2;
+                int cp = -1;
+                if (tid < carry) {
+                    c0 = s_stg[(head + tid) * 3 + 0];
+                    c1 = s_stg[(head + tid) * 3 + 1];
+                    c2 = s_stg[(head + tid) * 3 + 2];
+                    cp = s_row[head + tid];
+                }
                 __syncthreads();
-                if (tid < carry) s_list[tid] = v;
+                if (tid < carry) {
+                    s_stg[tid * 3 + 0] = c0;
+                    s_stg[tid * 3 + 1] = c1;
+                    s_stg[tid * 3 + 2] = c2;
+                    s_row[tid] = cp;
+                }
                 n_list = carry;
                 head = 0;
             }
-            for (int pass = 0; pass < SEG / TC_THREADS; ++pass) {
-                const int64_t e = seg + pass * TC_THREADS + tid;
+            {
+                const int64_t e = seg + tid;
                 bool keep = false;
+                int p = -1;
+                float4 s0, s1, s2;
                 if (e < e_end) {
-                    const int p = P.tile_rows[e];
+                    p = P.tile_rows[e];
                     if (P.d_off[p + 1] > P.d_off[p]) {   // rows without D entries add nothing
-                    const RowRec r = P.rec[p];
-                    const BandConst bc = P.bc[P.row_band[p]];
-                    const float hb = bc.h;
-                    const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
-                    const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
-                    const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
-                    keep = box_may_touch(cx, cy, cz, r.b.x, r.b.y, r.b.z, r.a.w, 3.5f * hb, 1.5f * hb, 1.5f * hb);
+                        const RowRec r = P.rec[p];
+                        const int b = P.row_band[p];
+                        const BandConst bc = P.bc[b];
+                        const float hb = bc.h;
+                        const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
+                        const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
+                        const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
+                        const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
+                        keep = box_may_touch(cx, cy, cz, ex, ey, ez, hl, 3.5f * hb, 1.5f * hb, 1.5f * hb);
+                        if (keep) {
+                            // is the whole sub-brick between the transducer planes?
+                            const float pext = 3.5f * hb * fabsf(ex) + 1.5f * hb * (fabsf(ey) + fabsf(ez)) + 1e-3f;
+                            const bool inner = fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl;
+                            const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
+                            s0 = P.ebase[e];
+                            s1 = make_float4(hb * ex, hb * ey, hb * ez, P.ebase3[e]);
+                            s2 = make_float4(r.b.w, __uint_as_float(tb), inner ? 1.0f : 0.0f, 0.0f);
+                        }
                     }
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
@@ -185,7 +214,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                     before += (w < warp) ? c : 0;
                     total += c;
                 }
-                if (keep) s_list[n_list + before + __popc(bal & ((1u << lane) - 1u))] = e;
+                if (keep) {
+                    const int pos = n_list + before + __popc(bal & ((1u << lane) - 1u));
+                    s_stg[pos * 3 + 0] = s0;
+                    s_stg[pos * 3 + 1] = s1;
+                    s_stg[pos * 3 + 2] = s2;
+                    s_row[pos] = p;
+                }
                 n_list += total;
                 __syncthreads();
             }
@@ -193,104 +228,107 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             // ---- 2. chunks of KC kept rows
             while (n_list - head >= KC || (last_seg && n_list - head > 0)) {
                 const int nrows = min(KC, n_list - head);
-                const int buf = chunk & 1;
+                const int buf = chunk % NSTAGE;
+                const int nbuf = (chunk + 1) % NSTAGE;
                 unsigned char* sA = sA0 + buf * a_bytes;
                 unsigned char* sB = sB0 + buf * b_bytes;
-                float4* stg = s_stg + buf * KC * 3;
-                int32_t* srow = s_row + buf * KC;
+                const float4* stg = s_stg + (size_t)head * 3;
+                const int32_t* srow = s_row + head;
                 if (chunk >= 2) {
-                    // the MMAs that last read this buffer must be done before it is rewritten
-                    if (!wait_phase(mbar0 + 8u * buf, (uint32_t)(((chunk >> 1) - 1) & 1))) {
+                    // MMAs complete in order: once chunk - 2 is done, A[buf] (last read by chunk - 3)
+                    // may be rewritten and B[nbuf] (last read by chunk - 2) may be cleared
+                    const int prev = chunk - 2;
+                    if (!wait_phase(mbar0 + 8u * (prev % NSTAGE), (uint32_t)((prev / NSTAGE) & 1))) {
                         if (tid == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
                         failed = true;
                     }
                 }
+                // (a failed wait is acted on at the barrier closing this chunk)
+                tc::fence_after_sync();
+                {
+                    uint4* b4 = reinterpret_cast<uint4*>(sB0 + nbuf * b_bytes);
+                    for (uint32_t i = tid; i < b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
+                }
+                // D entries of the chunk's rows (16 threads per row): load now, store after the
+                // generation below so that the global-load latency overlaps it
+                const int sr = tid >> 4, si0 = tid & 15;
+                const int sp = (sr < nrows) ? srow[sr] : -1;
+                int64_t d_lo = 0, d_hi = 0;
+                int j0 = -1, j1 = -1;
+                float w0 = 0.0f, w1 = 0.0f;
+                if (sp >= 0) {
+                    d_lo = P.d_off[sp];
+                    d_hi = P.d_off[sp + 1];
+                    if (d_lo + si0 < d_hi) {
+                        j0 = P.d_idx[d_lo + si0];
+                        w0 = P.d_val[d_lo + si0];
+                    }
+                    if (d_lo + si0 + 16 < d_hi) {
+                        j1 = P.d_idx[d_lo + si0 + 16];
+                        w1 = P.d_val[d_lo + si0 + 16];
+                    }
+                }
+                // generate A: rows 2 warp, 2 warp + 1; this lane's four voxels
+                {
+                    float vals[2][NX_LANE];
+#pragma unroll
+                    for (int rr = 0; rr < 2; ++rr) {
+                        const int r = 2 * warp + rr;
+                        if (r < nrows) {
+                            const float4 A4 = stg[r * 3 + 0];
+                            const float4 B4 = stg[r * 3 + 1];
+                            const float4 C4 = stg[r * 3 + 2];
+                            const float hx = B4.x, hy = B4.y, hz = B4.z;
+                            const float o = fmaf(Xv, hx, fmaf(Yv, hy, Zv * hz));
+                            const float psb = A4.x + o, prb = A4.y + o;
+                            const float c1 = fmaf(Yv, hz, fmaf(-Zv, hy, A4.z));
+                            const float c2 = fmaf(Zv, hx, fmaf(-Xv, hz, A4.w));
+                            const float c3 = fmaf(Xv, hy, fmaf(-Yv, hx, B4.w));
+                            const float c1sq = c1 * c1;
+                            const uint32_t tb = __float_as_uint(C4.y);
+                            const bool inner = C4.z != 0.0f;
+#pragma unroll
+                            for (int t = 0; t < NX_LANE; ++t) {
+                                const float ft = (float)t;
+                                const float pst = fmaf(ft, hx, psb), prt = fmaf(ft, hx, prb);
+                                const float c2t = fmaf(-ft, hz, c2), c3t = fmaf(ft, hy, c3);
+                                const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
+                                float is, ir;
+                                const float v = inner ? detour_v<FFT_DT_STABLE, true, true>(pst, prt, q2, 0.0f, is, ir)
+                                                      : detour_v<FFT_DT_STABLE, true, false>(pst, prt, q2, 0.0f, is, ir);
+                                vals[rr][t] = phi_lookup(v, tb, nm1) * (is * ir) * C4.x;
+                            }
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < NX_LANE; ++t) vals[rr][t] = 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < NX_LANE; ++t)
+                        *reinterpret_cast<uint32_t*>(sA + tc::kmajor_offset((uint32_t)(32 * t + lane),
+                                                                            (uint32_t)(2 * warp), KC)) =
+                            pack_bf16x2(vals[0][t], vals[1][t]);
+                }
+                // scatter the D entries (column j, chunk row sr) into B
+                if (j0 >= 0)
+                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)j0, (uint32_t)sr, KC)) =
+                        __float2bfloat16_rn(w0);
+                if (j1 >= 0)
+                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)j1, (uint32_t)sr, KC)) =
+                        __float2bfloat16_rn(w1);
+                if (sp >= 0) {
+                    for (int64_t i = d_lo + si0 + 32; i < d_hi; i += 16) {
+                        const int j = P.d_idx[i];
+                        *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)j, (uint32_t)sr, KC)) =
+                            __float2bfloat16_rn(P.d_val[i]);
+                    }
+                }
+                tc::fence_proxy_async_smem();
+                tc::fence_before_sync();
                 if (__syncthreads_or(failed)) {
                     failed = true;
                     break;
                 }
-                tc::fence_after_sync();
-                // stage rows (warp 0) and clear the B tile (everyone)
-                if (warp == 0) {
-                    int p = -1;
-                    float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
-                    if (lane < nrows) {
-                        const int64_t e = s_list[head + lane];
-                        p = P.tile_rows[e];
-                        const float4 base = P.ebase[e];
-                        const float base3 = P.ebase3[e];
-                        const RowRec r = P.rec[p];
-                        const int b = P.row_band[p];
-                        const BandConst bc = P.bc[b];
-                        const float hb = bc.h;
-                        const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
-                        // is the whole sub-brick between the transducer planes?
-                        const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
-                        const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
-                        const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
-                        const float pext = 3.5f * hb * fabsf(ex) + 1.5f * hb * (fabsf(ey) + fabsf(ez)) + 1e-3f;
-                        const bool inner = fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl;
-                        const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
-                        s0 = base;
-                        s1 = make_float4(hb * ex, hb * ey, hb * ez, base3);
-                        s2 = make_float4(r.b.w, __uint_as_float(tb), inner ? 1.0f : 0.0f, 0.0f);
-                    }
-                    stg[lane * 3 + 0] = s0;
-                    stg[lane * 3 + 1] = s1;
-                    stg[lane * 3 + 2] = s2;
-                    srow[lane] = p;
-                }
-                {
-                    uint4* b4 = reinterpret_cast<uint4*>(sB);
-                    for (uint32_t i = tid; i < b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
-                }
-                __syncthreads();
-                // scatter the kept rows' sparse D entries into B (column j, row r)
-                {
-                    const int r = tid >> 4, i0 = tid & 15;
-                    const int p = srow[r];
-                    if (p >= 0) {
-                        for (int64_t i = P.d_off[p] + i0; i < P.d_off[p + 1]; i += 16) {
-                            const int j = P.d_idx[i];
-                            *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)j, (uint32_t)r, KC)) =
-                                __float2bfloat16_rn(P.d_val[i]);
-                        }
-                    }
-                }
-                // generate A: this thread's voxel, rows 8 g .. 8 g + 7 of the chunk
-                {
-                    float vals[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int r = 8 * g + q;
-                        const float4 A4 = stg[r * 3 + 0];
-                        const float4 B4 = stg[r * 3 + 1];
-                        const float4 C4 = stg[r * 3 + 2];
-                        float val = 0.0f;
-                        if (r < nrows) {
-                            const float hx = B4.x, hy = B4.y, hz = B4.z;
-                            const float o = fmaf(Xv, hx, fmaf(Yv, hy, Zv * hz));
-                            const float ps = A4.x + o, pr = A4.y + o;
-                            const float c1 = fmaf(Yv, hz, fmaf(-Zv, hy, A4.z));
-                            const float c2 = fmaf(Zv, hx, fmaf(-Xv, hz, A4.w));
-                            const float c3 = fmaf(Xv, hy, fmaf(-Yv, hx, B4.w));
-                            const float q2 = fmaf(c1, c1, fmaf(c2, c2, c3 * c3));
-                            float is, ir, v;
-                            if (C4.z != 0.0f)
-                                v = detour_v<FFT_DT_STABLE, true, true>(ps, pr, q2, 0.0f, is, ir);
-                            else
-                                v = detour_v<FFT_DT_STABLE, true, false>(ps, pr, q2, 0.0f, is, ir);
-                            val = phi_lookup(v, __float_as_uint(C4.y), nm1) * (is * ir) * C4.x;
-                        }
-                        vals[q] = val;
-                    }
-                    uint4 packed = make_uint4(pack_bf16x2(vals[0], vals[1]), pack_bf16x2(vals[2], vals[3]),
-                                              pack_bf16x2(vals[4], vals[5]), pack_bf16x2(vals[6], vals[7]));
-                    *reinterpret_cast<uint4*>(sA + tc::kmajor_offset((uint32_t)m_row, (uint32_t)(8 * g), KC)) = packed;
-                }
-                tc::fence_proxy_async_smem();
-                tc::fence_before_sync();
-                __syncthreads();
                 tc::fence_after_sync();
                 if (tid == 0) {
                     const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
@@ -317,7 +355,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         // ---- 3. all MMAs of this unit done -> TMEM -> Y
         {
             const int last = chunk - 1;
-            if (!wait_phase(mbar0 + 8u * (last & 1), (uint32_t)((last >> 1) & 1))) {
+            if (!wait_phase(mbar0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1))) {
                 if (tid == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
                 failed = true;
             }
@@ -329,8 +367,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         tc::fence_after_sync();
         {
             const int quarter = warp & 3;              // TMEM lanes this warp may access
-            const int mm = 32 * quarter + lane;         // voxel m of the sub-brick
-            const int x = X0 + (mm & 7), y = Y0 + ((mm >> 3) & 3), z = Z0 + (mm >> 5);
+            // TMEM lane 32 quarter + lane holds voxel t = quarter of generation lane `lane`
+            const int x = X0 + 4 * (lane & 1) + quarter, y = Y0 + ((lane >> 1) & 3), z = Z0 + (lane >> 3);
             const bool valid = x < P.nx && y < P.ny && z < P.nz;
             const int64_t v = ((int64_t)z * P.ny + y) * P.nx + x;
             const int cols = P.nh * P.n_half;
@@ -348,10 +386,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         __syncthreads();
     }
     // drain: every issued MMA must be complete before the accumulator is released
-    if (chunk > 0) {
+    if (chunk > 0) {   // MMAs complete in order: the last one done means all are done
         const int last = chunk - 1;
-        wait_phase(mbar0 + 8u * (last & 1), (uint32_t)((last >> 1) & 1));
-        if (chunk > 1) wait_phase(mbar0 + 8u * ((last - 1) & 1), (uint32_t)(((last - 1) >> 1) & 1));
+        wait_phase(mbar0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1));
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -360,6 +397,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
 }
 
 }  // namespace
+
+static size_t psf_tc_smem(fft_geom g, int b_rows) {
+    return NSTAGE * (size_t)(128 * KC * 2) + NSTAGE * (size_t)b_rows * KC * 2 +
+           (((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15) +
+           (size_t)LIST_CAP * (3 * sizeof(float4) + sizeof(int32_t)) + sizeof(TcShared) + 1024;
+}
+
+// Largest number of right-hand sides one tensor-core launch can take on this device (the B
+// ring grows with it): a multiple of 16, at most 512; 0 if even 16 do not fit.
+int psf_tc_max_cols(fft_geom g) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int best = 0;
+    for (int c = 16; c <= 512; c += 16) {
+        const int nh = c > 256 ? 2 : 1;
+        const int n_half = (int)ceil_div(ceil_div(c, nh), 16) * 16;
+        if (psf_tc_smem(g, nh * n_half) <= (size_t)optin) best = c;
+    }
+    return best;
+}
 
 // Y = J^T D on the tensor cores for D given as sparse rows (d_off, d_idx, d_val) with n_rhs
 // columns (1 .. 512); column j of Y goes to out[col_map[j] * V + v]. out must be zeroed by the
@@ -431,10 +489,7 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     P.status = d_ctr + 1;
 
     // at least 120 KB so that only one CTA (which holds TMEM for the whole launch) fits on an SM
-    const size_t smem = std::max<size_t>(
-        120 * 1024, 2 * (size_t)(128 * KC * 2) + 2 * (size_t)P.b_rows * KC * 2 +
-                        (((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15) +
-                        2 * KC * 3 * sizeof(float4) + 2 * KC * sizeof(int32_t) + LIST_CAP * sizeof(int64_t));
+    const size_t smem = std::max<size_t>(120 * 1024, psf_tc_smem(g, P.b_rows) - sizeof(TcShared) - 1024);
     int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

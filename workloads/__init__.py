@@ -238,18 +238,18 @@ def slices3d() -> Workload:
                     C0_WATER, cg_iters=20, lambda_rel=1e-3, model_seed=6, noise_seed=7)
 
 
-def ring_subsets(n_tx: int = 256, n_slices: int = 16, strides=(4, 2, 1)) -> List[np.ndarray]:
-    """Row subsets of the ``slices3d`` pair list: every 4th / 2nd / every element of each ring.
+def ring_subsets(n_tx: int = 256, n_slices: int = 16, strides=(4, 2, 1), n_bands: int = 3) -> List[np.ndarray]:
+    """Row subsets of a (band, slice, s, r) pair list: every 4th / 2nd / every element of each ring.
 
     A pair belongs to a subset when both its elements are on the subset's stride. Returned
-    as sorted row-index arrays into the (band, slice, s, r) row order, for all 3 bands.
+    as sorted row-index arrays, for all bands (3 for ``slices3d``, 1 for ``ring256``).
     """
     ppr = n_tx * (n_tx - 1) // 2
     local = unordered_pairs(range(n_tx))
     out = []
     for st in strides:
         keep = np.flatnonzero((local[:, 0] % st == 0) & (local[:, 1] % st == 0))
-        rows = [b * n_slices * ppr + s * ppr + keep for b in range(3) for s in range(n_slices)]
+        rows = [b * n_slices * ppr + s * ppr + keep for b in range(n_bands) for s in range(n_slices)]
         out.append(np.concatenate(rows).astype(np.int32))
     return out
 
