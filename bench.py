@@ -45,7 +45,7 @@ FP32_LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) of one J^T apply-kernel launch on this workload, from the ncu
 # capture summarised in profiles/apply_kernel_ring256.md; None until captured for the
 # current kernel.
-APPLY_TRAFFIC_BYTES = None
+APPLY_TRAFFIC_BYTES = 117990656   # 100956160 read + 17034496 written (prof_jt3)
 
 
 def peaks():

@@ -286,18 +286,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                             const float c3 = fmaf(Xv, hy, fmaf(-Yv, hx, B4.w));
                             const float c1sq = c1 * c1;
                             const uint32_t tb = __float_as_uint(C4.y);
-                            const bool inner = C4.z != 0.0f;
-#pragma unroll
-                            for (int t = 0; t < NX_LANE; ++t) {
-                                const float ft = (float)t;
-                                const float pst = fmaf(ft, hx, psb), prt = fmaf(ft, hx, prb);
-                                const float c2t = fmaf(-ft, hz, c2), c3t = fmaf(ft, hy, c3);
-                                const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
-                                float is, ir;
-                                const float v = inner ? detour_v<FFT_DT_STABLE, true, true>(pst, prt, q2, 0.0f, is, ir)
-                                                      : detour_v<FFT_DT_STABLE, true, false>(pst, prt, q2, 0.0f, is, ir);
-                                vals[rr][t] = phi_lookup(v, tb, nm1) * (is * ir) * C4.x;
+                            // warp-uniform choice of the detour form for the whole run of voxels
+#define FFT_TC_RUN(INNER_V)                                                                        \
+    _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                        \
+        const float ft = (float)t;                                                               \
+        const float pst = fmaf(ft, hx, psb), prt = fmaf(ft, hx, prb);                            \
+        const float c2t = fmaf(-ft, hz, c2), c3t = fmaf(ft, hy, c3);                             \
+        const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                   \
+        float is, ir;                                                                            \
+        const float v = detour_v<FFT_DT_STABLE, true, INNER_V>(pst, prt, q2, 0.0f, is, ir);      \
+        vals[rr][t] = phi_lookup(v, tb, nm1) * (is * ir) * C4.x;                                 \
+    }
+                            if (C4.z != 0.0f) {
+                                FFT_TC_RUN(true)
+                            } else {
+                                FFT_TC_RUN(false)
                             }
+#undef FFT_TC_RUN
                         } else {
 #pragma unroll
                             for (int t = 0; t < NX_LANE; ++t) vals[rr][t] = 0.0f;
