@@ -188,8 +188,10 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                 const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
                 stg[lane * 3 + 0] = base;
                 stg[lane * 3 + 1] = make_float4(hb * ex, hb * ey, hb * ez, base3);
-                stg[lane * 3 + 2] =
-                    make_float4(W, __uint_as_float(tb), __int_as_float(p), __int_as_float(b | (bc.sharp << 8)));
+                // planar pair (both transducers at one z): stepping along x changes only c3
+                const int planar = (ez == 0.0f) ? 1 : 0;
+                stg[lane * 3 + 2] = make_float4(W, __uint_as_float(tb), __int_as_float(p),
+                                                __int_as_float(b | (bc.sharp << 8) | (planar << 9)));
             }
             const uint32_t m0 = __ballot_sync(0xffffffffu, ok0);
             const uint32_t m1 = __ballot_sync(0xffffffffu, ok1);
@@ -208,7 +210,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                 const float hl = 0.5f * (A.x - A.y);   // used by the textbook (NAIVE) detour only
                 const uint32_t tb = __float_as_uint(C.y);
                 // voxels whose FP32 detour falls within CUT_BAND of a sharp band's cut-off
-                const float cutb = (SHARP && (__float_as_int(C.w) >> 8)) ? CUT_BAND : -1.0f;
+                const float cutb = (SHARP && ((__float_as_int(C.w) >> 8) & 1)) ? CUT_BAND : -1.0f;
+                const bool planar = (DT != FFT_DT_FP64) && ((__float_as_int(C.w) >> 9) & 1);
                 uint32_t fix = 0;
                 // lane base (sub-brick 0, t = 0) in the pair frame: small offsets added to the
                 // tile origin's FP64-derived values
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                     if (!((ms >> bit) & 1u)) continue;
                     const float c1sq = c1 * c1;
                     const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
-#define FFT_EVAL_SUB(INNER_V)                                                                        \
+#define FFT_EVAL_SUB(INNER_V, PLANAR_V)                                                              \
     _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                          \
         const float ft = (float)t;                                                                 \
         float is, ir, v, w;                                                                        \
@@ -244,9 +247,14 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
         } else {                                                                                   \
             const float pst = fmaf(ft, hx, psb);                                                   \
             const float prt = fmaf(ft, hx, prb);                                                   \
-            const float c2t = fmaf(-ft, hz, c2);                                                   \
             const float c3t = fmaf(ft, hy, c3);                                                    \
-            const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                 \
+            float q2;                                                                              \
+            if (PLANAR_V) {                                                                        \
+                q2 = fmaf(c3t, c3t, c12sq);                                                        \
+            } else {                                                                               \
+                const float c2t = fmaf(-ft, hz, c2);                                               \
+                q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                         \
+            }                                                                                      \
             if (SHARP) {                                                                           \
                 v = detour_v<DT, GUARD, INNER_V, true>(pst, prt, q2, hl, is, ir);                  \
                 if (fabsf(v - 1.0f) < cutb) fix |= 1u << (4 * s + t);                              \
@@ -269,10 +277,19 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
             if ((vmask >> (4 * s + t)) & 1u) part = fmaf(val, val, part);                          \
         }                                                                                          \
     }
+                    const float c12sq = fmaf(c2, c2, c1sq);
                     if (inner) {
-                        FFT_EVAL_SUB(true)
+                        if (planar) {
+                            FFT_EVAL_SUB(true, true)
+                        } else {
+                            FFT_EVAL_SUB(true, false)
+                        }
                     } else {
-                        FFT_EVAL_SUB(false)
+                        if (planar) {
+                            FFT_EVAL_SUB(false, true)
+                        } else {
+                            FFT_EVAL_SUB(false, false)
+                        }
                     }
 #undef FFT_EVAL_SUB
                 }
@@ -301,9 +318,14 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                             const float c1sq = c1s * c1s;
                             const float pst = fmaf(ft, hx, pss);
                             const float prt = fmaf(ft, hx, prs);
-                            const float c2t = fmaf(-ft, hz, c2s);
                             const float c3t = fmaf(ft, hy, c3s);
-                            const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
+                            float q2;
+                            if (planar) {
+                                q2 = fmaf(c3t, c3t, fmaf(c2s, c2s, c1sq));
+                            } else {
+                                const float c2t = fmaf(-ft, hz, c2s);
+                                q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
+                            }
                             const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
                             float is, ir;
                             const float v = __saturatef(inner ? detour_v<DT, GUARD, true, true>(pst, prt, q2, hl, is, ir)

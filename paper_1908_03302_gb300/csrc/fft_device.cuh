@@ -123,14 +123,25 @@ __device__ __forceinline__ float jentry_f32(const RowRec& r, const BandConst& c,
                                             int n_tab, const RowRec64* rec64, int p, double ox, double oy,
                                             double oz, double h64, int ix, int iy, int iz, bool naive);
 
-// Table lookup with linear interpolation: Phi(v) for v in [0, 1], tb the shared-memory byte
-// address of the band table minus (MAGIC bits << 3); nm1 = n_tab - 1. floor(v nm1) comes
-// from a round-down add of MAGIC, whose bit pattern then indexes the table directly.
+// Table lookup with linear interpolation, Phi(v) for the normalised detour v in [0, 1].
+// Entry k of a band table holds (Phi_k - k dPhi_k, nm1 dPhi_k) with dPhi_k = Phi_{k+1} - Phi_k
+// and nm1 = n_tab - 1, so that on [k, k + 1) / nm1 the interpolant is one FFMA in v:
+//   Phi_k + (v nm1 - k) dPhi_k = (Phi_k - k dPhi_k) + v (nm1 dPhi_k).
+// k = floor(v nm1) comes from a round-down add of MAGIC, whose bit pattern then addresses the
+// table directly: tb is the shared-memory byte address of the band table minus (MAGIC bits << 3).
 __device__ __forceinline__ float phi_lookup(float v, uint32_t tb, float nm1) {
-    float tt = __fmaf_rd(v, nm1, MAGIC);
-    float fr = fmaf(v, nm1, MAGIC - tt);
-    float2 T = lds_f2(tb + (__float_as_uint(tt) << 3));
-    return fmaf(fr, T.y, T.x);
+    const float tt = __fmaf_rd(v, nm1, MAGIC);
+    const float2 T = lds_f2(tb + (__float_as_uint(tt) << 3));
+    return fmaf(v, T.y, T.x);
+}
+
+// The same from a band table in global memory (n_tab entries).
+__device__ __forceinline__ float phi_lookup_global(float v, const float2* __restrict__ tab, int n_tab) {
+    const float tt = __fmaf_rd(v, (float)(n_tab - 1), MAGIC);
+    int k = (int)(__float_as_uint(tt) - 0x4B400000u);
+    k = k < 0 ? 0 : (k > n_tab - 1 ? n_tab - 1 : k);
+    const float2 T = tab[k];
+    return fmaf(v, T.y, T.x);
 }
 
 }  // namespace fftgb
@@ -152,12 +163,6 @@ __device__ __forceinline__ float jentry_f32(const RowRec& r, const BandConst& c,
     if (c.sharp && rec64 && fabsf(vv - 1.0f) < CUT_BAND)
         vv = settle_cut(__saturatef(vv), in_support64(rec64[p], ox, oy, oz, h64, ix, iy, iz, c.U));
     vv = __saturatef(vv);
-    const float nm1 = (float)(n_tab - 1);
-    const float u = vv * nm1;
-    int k = (int)floorf(u);
-    if (k > n_tab - 1) k = n_tab - 1;
-    if (k < 0) k = 0;
-    const float2 T = tab[k];
-    return fmaf(u - (float)k, T.y, T.x) * (is * ir) * r.b.w;
+    return phi_lookup_global(vv, tab, n_tab) * (is * ir) * r.b.w;
 }
 }  // namespace fftgb

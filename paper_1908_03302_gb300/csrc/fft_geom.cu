@@ -152,12 +152,14 @@ __global__ void row_sort_kernel(const int64_t* __restrict__ row_off, int64_t M, 
 __global__ void pack_table_kernel(const double* __restrict__ phi, int n, float2* __restrict__ out) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    // Entry k holds (Phi_k, Phi_{k+1} - Phi_k). The last entry is the cut-off: Phi = 0 at and
-    // beyond dt_max (hard truncation), so it holds (0, 0).
+    // Entry k holds (Phi_k - k dPhi_k, (n - 1) dPhi_k), dPhi_k = Phi_{k+1} - Phi_k, formed in FP64:
+    // the interpolant on [k, k + 1) is then one FFMA in the normalised detour. The last entry
+    // is the cut-off: Phi = 0 at and beyond dt_max (hard truncation), so it holds (0, 0).
     if (k == n - 1) {
         out[k] = make_float2(0.0f, 0.0f);
     } else {
-        out[k] = make_float2((float)phi[k], (float)(phi[k + 1] - phi[k]));
+        const double d = phi[k + 1] - phi[k];
+        out[k] = make_float2((float)(phi[k] - (double)k * d), (float)(d * (double)(n - 1)));
     }
 }
 

@@ -46,14 +46,7 @@ __global__ void column_kernel(const RowRec* __restrict__ rec, const int32_t* __r
     if (c.sharp && fabsf(vv - 1.0f) < CUT_BAND)   // decide the cut of a sharp band in FP64
         vv = settle_cut(__saturatef(vv), in_support64(rec64[p], org64.x, org64.y, org64.z, h64, ix, iy, iz, c.U));
     vv = __saturatef(vv);
-    const float nm1 = (float)(n_tab - 1);
-    const float u = vv * nm1;
-    int k = (int)floorf(u);
-    if (k > n_tab - 1) k = n_tab - 1;
-    if (k < 0) k = 0;
-    const float2 T = tab[(int64_t)b * n_tab + k];
-    const float phi = fmaf(u - (float)k, T.y, T.x);
-    D[p] = phi * (is * ir) * r.b.w;
+    D[p] = phi_lookup_global(vv, tab + (int64_t)b * n_tab, n_tab) * (is * ir) * r.b.w;
 }
 
 // mask[rows[i]] |= 1 << s: row membership of subset s.
