@@ -179,6 +179,11 @@ fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, co
         off[0] = 0;
         for (int64_t p = 0; p < g->M; ++p) off[p + 1] = off[p] + cnt[p];
         const int64_t nnz = off[g->M];
+        if (nnz > (int64_t)UINT32_MAX) {   // the kernel keeps 32-bit offsets into D
+            rc = FFT_ERR_ARG;
+            set_error("fft_psf_batch: more than 2^32 - 1 non-zeros in one block of D; use fewer spikes per call");
+            break;
+        }
         cudaFree(d_idx);
         cudaFree(d_val);
         d_idx = nullptr;

@@ -6,17 +6,20 @@
 // for an 8 x 4 x 4 sub-brick (128 voxels = the MMA's M) the rows whose support reaches it are
 // the contraction dimension K and the (subset, spike) columns are N.
 //
-// Per CTA (one per SM, 16 warps) and sub-brick:
+// Per CTA (one per SM; 16 generator warps and one MMA warp) and sub-brick:
 //   1. scan the tile's candidate rows, keep those that may reach the sub-brick (tangent-plane
-//      bound of the convex detour), compact them in shared memory;
-//   2. for every chunk of 32 kept rows: warp 0 stages the rows' pair-frame data, all warps
-//      clear the B tile and scatter the rows' sparse D entries into it (BF16), then generate
-//      the A tile J[p, v] (FP32 evaluation as in the J^T kernel, rounded to BF16); one thread
-//      issues tcgen05.mma (M = 128, N = up to 2 x 256, K = 32) accumulating in TMEM and
-//      commits to the buffer's mbarrier; A / B / staging are double-buffered, so generation
-//      of chunk c + 1 overlaps the MMAs of chunk c;
+//      bound of the convex detour), stage their pair-frame data in shared memory;
+//   2. for every chunk of 32 kept rows, generator warp w owns rows 2w and 2w + 1: it clears the
+//      sparse D entries it wrote into the chunk's B buffer three chunks earlier, scatters the
+//      rows' D entries (BF16), generates its two rows of the A tile J[p, v] (FP32 evaluation as
+//      in the J^T kernel, rounded to BF16) and arrives on the buffer's "full" mbarrier; the MMA
+//      warp waits for it, issues tcgen05.mma (M = 128, N = up to 2 x 256, K = 32) accumulating
+//      in TMEM and commits to the buffer's "empty" mbarrier, which the generators wait for
+//      before they reuse the buffer. Three A / B buffers and no CTA-wide barrier per chunk let
+//      generation run up to three chunks ahead of the tensor cores;
 //   3. after the last chunk, TMEM -> registers -> Y.
-// Every wait is bounded; a time-out sets a status word and the kernel drains and returns.
+// Every wait is bounded; a thread whose wait timed out sets a status word and waits no more,
+// and the CTA stops at the end of the sub-brick.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -32,12 +35,14 @@ namespace fftgb {
 
 namespace {
 
-constexpr int TC_WARPS = 16;
+constexpr int GEN_WARPS = 16;          // warps that generate J and scatter D
+constexpr int TC_WARPS = GEN_WARPS + 1;    // + one warp that issues the MMAs
 constexpr int TC_THREADS = TC_WARPS * 32;
-constexpr int KC = 32;                 // rows per chunk (MMA K per chunk)
+constexpr int KC = 32;                 // rows per chunk (MMA K per chunk): 2 per generator warp
 constexpr int NSTAGE = 3;              // A / B buffers in the ring
 constexpr int SEG = TC_THREADS;        // tile entries scanned per pass (one per thread)
 constexpr int LIST_CAP = SEG + KC;     // kept rows waiting for a chunk (staged records)
+constexpr int D_LANES = 16;            // lanes that scatter one row's D entries
 constexpr long long WAIT_BUDGET = 4000000000ll;   // cycles (~2 s)
 
 struct PsfTcParams {
@@ -70,11 +75,11 @@ struct PsfTcParams {
 };
 
 struct TcShared {
-    unsigned long long mbar[NSTAGE];
+    unsigned long long full[NSTAGE];    // generator warps -> MMA warp (GEN_WARPS arrivals)
+    unsigned long long empty[NSTAGE];   // MMA warp -> generator warps (tcgen05.commit)
     uint32_t tmem_slot;
     int unit;
     int wcnt[TC_WARPS];
-    int n_list;
 };
 
 __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
@@ -94,8 +99,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ TcShared S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool is_gen = warp < GEN_WARPS;
 
-    // ---- shared-memory carve-up: A[2], B[2] (1 KB aligned), table, staging, row list
+    // ---- shared-memory carve-up: A[NSTAGE], B[NSTAGE] (1 KB aligned), table, staged row list
     const uint32_t a_bytes = 128u * KC * 2u;
     const uint32_t b_bytes = (uint32_t)P.b_rows * KC * 2u;
     unsigned char* sA0 = smem;
@@ -104,37 +110,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
     float2* s_tab = reinterpret_cast<float2*>(smem + off);
     off += ((size_t)P.n_bands * P.n_tab * sizeof(float2) + 15) & ~(size_t)15;
     float4* s_stg = reinterpret_cast<float4*>(smem + off);          // [LIST_CAP][3] staged kept rows
-    off += (size_t)LIST_CAP * 3 * sizeof(float4);
-    int32_t* s_row = reinterpret_cast<int32_t*>(smem + off);        // [LIST_CAP] their row indices
 
     for (int i = tid; i < P.n_bands * P.n_tab; i += TC_THREADS) s_tab[i] = P.tab[i];
+    {   // B buffers start cleared; afterwards each generator lane clears the entries it wrote
+        uint4* b4 = reinterpret_cast<uint4*>(sB0);
+        for (uint32_t i = tid; i < NSTAGE * b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
+    }
     const uint32_t tab_addr = smem_addr(s_tab);
     const float nm1 = (float)(P.n_tab - 1);
-    const uint32_t mbar0 = smem_addr(&S.mbar[0]);
+    const uint32_t full0 = smem_addr(&S.full[0]), empty0 = smem_addr(&S.empty[0]);
     if (warp == 0) {
         tc::tmem_alloc(smem_addr(&S.tmem_slot), (uint32_t)P.tmem_cols);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int b = 0; b < NSTAGE; ++b) tc::mbar_init(mbar0 + 8u * b, 1);
+        for (int b = 0; b < NSTAGE; ++b) {
+            tc::mbar_init(full0 + 8u * b, GEN_WARPS);
+            tc::mbar_init(empty0 + 8u * b, 1);
+        }
     }
-    {   // every B buffer starts cleared; afterwards each is cleared one chunk ahead of its use
-        uint4* b4 = reinterpret_cast<uint4*>(sB0);
-        for (uint32_t i = tid; i < NSTAGE * b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
-    }
+    tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t taddr = S.tmem_slot;
     const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)P.n_half);
 
-    int chunk = 0;        // chunks issued by this CTA so far (selects buffer and mbarrier phase)
+    int chunk = 0;        // chunks issued by this CTA so far (selects buffer and mbarrier phases)
     bool failed = false;
     // Generation role: warp w evaluates rows 2w and 2w + 1 of a chunk; lane l owns the four
     // consecutive x voxels (4 lx + t, ly, lz), t = 0..3, of the 8 x 4 x 4 sub-brick, with
     // lx = l & 1, ly = (l >> 1) & 3, lz = l >> 3. Voxel t of lane l is MMA row (TMEM lane)
     // m = 32 t + l, which spreads a warp's stores over all eight 16-byte slots of a core matrix.
+    // For D the warp owns B-tile rows 2w (lanes 0-15) and 2w + 1 (lanes 16-31) of every buffer;
+    // lane i of a half scatters the row's D entries i and i + 16 (more, rarely, in a loop).
     const int glx = lane & 1, gly = (lane >> 1) & 3, glz = lane >> 3;
+    const int d_r = 2 * warp + (lane >> 4), d_i0 = lane & (D_LANES - 1);
+    // D positions this lane wrote into the buffer of the current chunk, of the next one and of
+    // the one after (the buffers rotate with the chunks): (j0 + 1) | (j1 + 1) << 10, bit 20 if
+    // the row had more than 2 D_LANES entries (then the lane clears its whole share of the row)
+    uint32_t old0 = 0, old1 = 0, old2 = 0;
 
     for (;;) {
         __syncthreads();   // everyone has read the previous unit index before it is replaced
@@ -156,22 +171,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         for (int64_t seg = e_begin; seg < e_end; seg += SEG) {
             // ---- 1. scan: keep rows that may reach the sub-brick, staged in the row list;
             //         the rows left over from the previous pass move to the front first
+            __syncthreads();   // every warp is done with the list entries of earlier chunks
             if (head > 0) {
                 const int carry = n_list - head;
                 float4 c0, c1, c2;
-                int cp = -1;
                 if (tid < carry) {
                     c0 = s_stg[(head + tid) * 3 + 0];
                     c1 = s_stg[(head + tid) * 3 + 1];
                     c2 = s_stg[(head + tid) * 3 + 2];
-                    cp = s_row[head + tid];
                 }
                 __syncthreads();
                 if (tid < carry) {
                     s_stg[tid * 3 + 0] = c0;
                     s_stg[tid * 3 + 1] = c1;
                     s_stg[tid * 3 + 2] = c2;
-                    s_row[tid] = cp;
                 }
                 n_list = carry;
                 head = 0;
@@ -179,11 +192,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             {
                 const int64_t e = seg + tid;
                 bool keep = false;
-                int p = -1;
                 float4 s0, s1, s2;
                 if (e < e_end) {
-                    p = P.tile_rows[e];
-                    if (P.d_off[p + 1] > P.d_off[p]) {   // rows without D entries add nothing
+                    const int p = P.tile_rows[e];
+                    const int64_t d0 = P.d_off[p], d1 = P.d_off[p + 1];
+                    if (d1 > d0) {   // rows without D entries add nothing
                         const RowRec r = P.rec[p];
                         const int b = P.row_band[p];
                         const BandConst bc = P.bc[b];
@@ -194,13 +207,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                         const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
                         keep = box_may_touch(cx, cy, cz, ex, ey, ez, hl, 3.5f * hb, 1.5f * hb, 1.5f * hb);
                         if (keep) {
-                            // is the whole sub-brick between the transducer planes?
+                            // is the whole sub-brick between the transducer planes? a planar pair?
                             const float pext = 3.5f * hb * fabsf(ex) + 1.5f * hb * (fabsf(ey) + fabsf(ez)) + 1e-3f;
                             const bool inner = fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl;
-                            const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
+                            // table base (a multiple of 8) with the inner / planar flags in bits 0, 1
+                            const uint32_t tb = (tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8) |
+                                                (inner ? 1u : 0u) | (ez == 0.0f ? 2u : 0u);
                             s0 = P.ebase[e];
                             s1 = make_float4(hb * ex, hb * ey, hb * ez, P.ebase3[e]);
-                            s2 = make_float4(r.b.w, __uint_as_float(tb), inner ? 1.0f : 0.0f, 0.0f);
+                            s2 = make_float4(r.b.w, __uint_as_float(tb), __uint_as_float((uint32_t)d0),
+                                             __int_as_float((int)(d1 - d0)));
                         }
                     }
                 }
@@ -219,57 +235,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                     s_stg[pos * 3 + 0] = s0;
                     s_stg[pos * 3 + 1] = s1;
                     s_stg[pos * 3 + 2] = s2;
-                    s_row[pos] = p;
                 }
                 n_list += total;
                 __syncthreads();
             }
             const bool last_seg = seg + SEG >= e_end;
-            // ---- 2. chunks of KC kept rows
+            // ---- 2. chunks of KC kept rows: no CTA-wide barrier, only the two mbarrier rings
             while (n_list - head >= KC || (last_seg && n_list - head > 0)) {
                 const int nrows = min(KC, n_list - head);
                 const int buf = chunk % NSTAGE;
-                const int nbuf = (chunk + 1) % NSTAGE;
+                const uint32_t use = (uint32_t)(chunk / NSTAGE);   // use count of this buffer
                 unsigned char* sA = sA0 + buf * a_bytes;
                 unsigned char* sB = sB0 + buf * b_bytes;
-                const float4* stg = s_stg + (size_t)head * 3;
-                const int32_t* srow = s_row + head;
-                if (chunk >= 2) {
-                    // MMAs complete in order: once chunk - 2 is done, A[buf] (last read by chunk - 3)
-                    // may be rewritten and B[nbuf] (last read by chunk - 2) may be cleared
-                    const int prev = chunk - 2;
-                    if (!wait_phase(mbar0 + 8u * (prev % NSTAGE), (uint32_t)((prev / NSTAGE) & 1))) {
-                        if (tid == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
-                        failed = true;
+                if (is_gen) {
+                    const float4* stg = s_stg + (size_t)head * 3;
+                    if (chunk >= NSTAGE && !failed) {   // the MMAs that last read this buffer must be done
+                        if (!wait_phase(empty0 + 8u * buf, (use - 1u) & 1u)) {
+                            if (lane == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
+                            failed = true;
+                        }
                     }
-                }
-                // (a failed wait is acted on at the barrier closing this chunk)
-                tc::fence_after_sync();
-                {
-                    uint4* b4 = reinterpret_cast<uint4*>(sB0 + nbuf * b_bytes);
-                    for (uint32_t i = tid; i < b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
-                }
-                // D entries of the chunk's rows (16 threads per row): load now, store after the
-                // generation below so that the global-load latency overlaps it
-                const int sr = tid >> 4, si0 = tid & 15;
-                const int sp = (sr < nrows) ? srow[sr] : -1;
-                int64_t d_lo = 0, d_hi = 0;
-                int j0 = -1, j1 = -1;
-                float w0 = 0.0f, w1 = 0.0f;
-                if (sp >= 0) {
-                    d_lo = P.d_off[sp];
-                    d_hi = P.d_off[sp + 1];
-                    if (d_lo + si0 < d_hi) {
-                        j0 = P.d_idx[d_lo + si0];
-                        w0 = P.d_val[d_lo + si0];
+                    // D entries of this lane's B row: loads issued now, stored after the generation
+                    uint32_t d_beg = 0;
+                    int d_cnt = 0;
+                    if (d_r < nrows) {
+                        const float4 C = stg[d_r * 3 + 2];
+                        d_beg = __float_as_uint(C.z);
+                        d_cnt = __float_as_int(C.w);
                     }
-                    if (d_lo + si0 + 16 < d_hi) {
-                        j1 = P.d_idx[d_lo + si0 + 16];
-                        w1 = P.d_val[d_lo + si0 + 16];
+                    const bool has0 = d_i0 < d_cnt, has1 = d_i0 + D_LANES < d_cnt;
+                    uint32_t j0 = 0, j1 = 0;
+                    float dv0 = 0.0f, dv1 = 0.0f;
+                    if (has0) {
+                        j0 = P.d_idx[d_beg + d_i0];
+                        dv0 = P.d_val[d_beg + d_i0];
                     }
-                }
-                // generate A: rows 2 warp, 2 warp + 1; this lane's four voxels
-                {
+                    if (has1) {
+                        j1 = P.d_idx[d_beg + d_i0 + D_LANES];
+                        dv1 = P.d_val[d_beg + d_i0 + D_LANES];
+                    }
+                    // generate A: rows 2 warp, 2 warp + 1; this lane's four voxels
                     float vals[2][NX_LANE];
 #pragma unroll
                     for (int rr = 0; rr < 2; ++rr) {
@@ -285,22 +290,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                             const float c2 = fmaf(Zv, hx, fmaf(-Xv, hz, A4.w));
                             const float c3 = fmaf(Xv, hy, fmaf(-Yv, hx, B4.w));
                             const float c1sq = c1 * c1;
-                            const uint32_t tb = __float_as_uint(C4.y);
+                            const float c12sq = fmaf(c2, c2, c1sq);
+                            const uint32_t tbf = __float_as_uint(C4.y);
+                            const uint32_t tb = tbf & ~3u;
                             // warp-uniform choice of the detour form for the whole run of voxels
-#define FFT_TC_RUN(INNER_V)                                                                        \
+#define FFT_TC_RUN(INNER_V, PLANAR_V)                                                              \
     _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                        \
         const float ft = (float)t;                                                               \
         const float pst = fmaf(ft, hx, psb), prt = fmaf(ft, hx, prb);                            \
-        const float c2t = fmaf(-ft, hz, c2), c3t = fmaf(ft, hy, c3);                             \
-        const float q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                   \
+        const float c3t = fmaf(ft, hy, c3);                                                      \
+        float q2;                                                                                \
+        if (PLANAR_V) {                                                                          \
+            q2 = fmaf(c3t, c3t, c12sq);                                                          \
+        } else {                                                                                 \
+            const float c2t = fmaf(-ft, hz, c2);                                                 \
+            q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                           \
+        }                                                                                        \
         float is, ir;                                                                            \
         const float v = detour_v<FFT_DT_STABLE, true, INNER_V>(pst, prt, q2, 0.0f, is, ir);      \
         vals[rr][t] = phi_lookup(v, tb, nm1) * (is * ir) * C4.x;                                 \
     }
-                            if (C4.z != 0.0f) {
-                                FFT_TC_RUN(true)
+                            if (tbf & 1u) {
+                                if (tbf & 2u) {
+                                    FFT_TC_RUN(true, true)
+                                } else {
+                                    FFT_TC_RUN(true, false)
+                                }
                             } else {
-                                FFT_TC_RUN(false)
+                                if (tbf & 2u) {
+                                    FFT_TC_RUN(false, true)
+                                } else {
+                                    FFT_TC_RUN(false, false)
+                                }
                             }
 #undef FFT_TC_RUN
                         } else {
@@ -313,29 +334,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                         *reinterpret_cast<uint32_t*>(sA + tc::kmajor_offset((uint32_t)(32 * t + lane),
                                                                             (uint32_t)(2 * warp), KC)) =
                             pack_bf16x2(vals[0][t], vals[1][t]);
-                }
-                // scatter the D entries (column j, chunk row sr) into B
-                if (j0 >= 0)
-                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)j0, (uint32_t)sr, KC)) =
-                        __float2bfloat16_rn(w0);
-                if (j1 >= 0)
-                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)j1, (uint32_t)sr, KC)) =
-                        __float2bfloat16_rn(w1);
-                if (sp >= 0) {
-                    for (int64_t i = d_lo + si0 + 32; i < d_hi; i += 16) {
-                        const int j = P.d_idx[i];
-                        *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)j, (uint32_t)sr, KC)) =
-                            __float2bfloat16_rn(P.d_val[i]);
+                    // B: clear what this lane wrote into the buffer three chunks ago, then scatter
+                    if (old0 & (1u << 20)) {
+                        for (int j = d_i0; j < P.b_rows; j += D_LANES)
+                            *reinterpret_cast<uint16_t*>(sB + tc::kmajor_offset((uint32_t)j, (uint32_t)d_r, KC)) = 0;
+                    } else {
+                        if (old0 & 0x3FFu)
+                            *reinterpret_cast<uint16_t*>(sB + tc::kmajor_offset((old0 & 0x3FFu) - 1u, (uint32_t)d_r, KC)) = 0;
+                        if ((old0 >> 10) & 0x3FFu)
+                            *reinterpret_cast<uint16_t*>(
+                                sB + tc::kmajor_offset(((old0 >> 10) & 0x3FFu) - 1u, (uint32_t)d_r, KC)) = 0;
                     }
-                }
-                tc::fence_proxy_async_smem();
-                tc::fence_before_sync();
-                if (__syncthreads_or(failed)) {
-                    failed = true;
-                    break;
-                }
-                tc::fence_after_sync();
-                if (tid == 0) {
+                    __syncwarp();   // another lane of the half may write where this one cleared
+                    if (has0)
+                        *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j0, (uint32_t)d_r, KC)) =
+                            __float2bfloat16_rn(dv0);
+                    if (has1)
+                        *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j1, (uint32_t)d_r, KC)) =
+                            __float2bfloat16_rn(dv1);
+                    for (int i = d_i0 + 2 * D_LANES; i < d_cnt; i += D_LANES)   // long rows (rare)
+                        *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)P.d_idx[d_beg + i],
+                                                                                 (uint32_t)d_r, KC)) =
+                            __float2bfloat16_rn(P.d_val[d_beg + i]);
+                    const uint32_t now = d_cnt > 2 * D_LANES ? (1u << 20)
+                                                             : (has0 ? j0 + 1u : 0u) | ((has1 ? j1 + 1u : 0u) << 10);
+                    old0 = old1;
+                    old1 = old2;
+                    old2 = now;
+                    // publish this warp's part of the chunk to the MMA warp
+                    tc::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(full0 + 8u * buf);
+                } else if (lane == 0) {
+                    // MMA warp: wait until all generator warps have written the chunk, then issue
+                    if (!failed && !wait_phase(full0 + 8u * buf, use & 1u)) {
+                        atomicExch(P.status, FFT_ERR_TIMEOUT);
+                        failed = true;
+                    }
+                    tc::fence_after_sync();
                     const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
 #pragma unroll
                     for (int ks = 0; ks < KC / 16; ++ks) {
@@ -347,30 +383,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                                          (unit_chunks > 0 || ks > 0) ? 1u : 0u);
                         }
                     }
-                    tc::mma_commit(mbar0 + 8u * buf);
+                    tc::mma_commit(empty0 + 8u * buf);
                 }
                 ++chunk;
                 ++unit_chunks;
                 head += nrows;
             }
-            if (failed) break;
         }
-        if (failed) break;
+        if (__syncthreads_or(failed)) break;
         if (unit_chunks == 0) continue;
         // ---- 3. all MMAs of this unit done -> TMEM -> Y
         {
             const int last = chunk - 1;
-            if (!wait_phase(mbar0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1))) {
+            if (!wait_phase(empty0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1))) {
                 if (tid == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
                 failed = true;
             }
         }
-        if (__syncthreads_or(failed)) {
-            failed = true;
-            break;
-        }
+        if (__syncthreads_or(failed)) break;
         tc::fence_after_sync();
-        {
+        if (is_gen) {
             const int quarter = warp & 3;              // TMEM lanes this warp may access
             // TMEM lane 32 quarter + lane holds voxel t = quarter of generation lane `lane`
             const int x = X0 + 4 * (lane & 1) + quarter, y = Y0 + ((lane >> 1) & 3), z = Z0 + (lane >> 3);
@@ -388,12 +420,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             }
         }
         tc::fence_before_sync();
-        __syncthreads();
     }
     // drain: every issued MMA must be complete before the accumulator is released
     if (chunk > 0) {   // MMAs complete in order: the last one done means all are done
         const int last = chunk - 1;
-        wait_phase(mbar0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1));
+        wait_phase(empty0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1));
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -406,7 +437,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
 static size_t psf_tc_smem(fft_geom g, int b_rows) {
     return NSTAGE * (size_t)(128 * KC * 2) + NSTAGE * (size_t)b_rows * KC * 2 +
            (((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15) +
-           (size_t)LIST_CAP * (3 * sizeof(float4) + sizeof(int32_t)) + sizeof(TcShared) + 1024;
+           (size_t)LIST_CAP * 3 * sizeof(float4) + sizeof(TcShared) + 1024;
 }
 
 // Largest number of right-hand sides one tensor-core launch can take on this device (the B

@@ -95,6 +95,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
+// One arrival on the mbarrier (release semantics for this thread's prior shared-memory writes).
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar)
+        : "memory");
+}
+
 // Bounded wait for the phase with the given parity; returns false if it did not complete
 // within `max_iter` polls (the caller then records an error instead of hanging).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, uint32_t max_iter) {
