@@ -45,7 +45,7 @@ FP32_LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) of one J^T apply-kernel launch on this workload, from the ncu
 # capture summarised in profiles/apply_kernel_ring256.md; None until captured for the
 # current kernel.
-APPLY_TRAFFIC_BYTES = 117990656   # 100956160 read + 17034496 written (prof_jt3)
+APPLY_TRAFFIC_BYTES = 118273024   # 101286912 read + 16986112 written (ncu, one J^T launch on ring256)
 
 
 def peaks():
@@ -141,17 +141,27 @@ def max_over_ranks(x: float, ws: int) -> float:
 
 # --------------------------------------------------------------------------- CPU oracle legs
 
-def oracle_sample_rate(w, n_rows: int, seed: int = 0):
-    """FP64 oracle J on a random row sample: (in-support evals/s, seconds, rows, threads)."""
+def oracle_leg(w, n_rows: int, n_vox: int, d_gpu, r_host, g_gpu, seed: int = 0):
+    """The FP64 oracle on a bounded sample of the workload: J on n_rows random rows (timed:
+    in-support evals/s on the host cores) and J^T on n_vox random voxels. Returns the
+    cpu_baseline record and the relative L2 errors of the GPU's J and J^T on the sample."""
     import oracle
     og = oracle.Geometry.from_workload(w)
-    rows = np.sort(np.random.default_rng(seed).choice(og.M, n_rows, replace=False)).astype(np.int64)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(og.M, n_rows, replace=False)).astype(np.int64)
+    vox = np.sort(rng.choice(og.V, n_vox, replace=False)).astype(np.int64)
     units = og.count_support(rows)
     m = wl.model_for(w)
     t0 = time.perf_counter()
-    og.J(m, rows)
-    dt = time.perf_counter() - t0
-    return units / dt, dt, units, oracle.n_threads()
+    d_ref = og.J(m, rows)
+    secs = time.perf_counter() - t0
+    g_ref = og.JT(r_host, vox)
+    cpu = {"value": units / secs, "unit": UNIT, "cores": oracle.n_threads(), "kind": "oracle",
+           "sample": f"FP64 oracle J on {n_rows} random rows of {w.name} ({units} in-support evals, {secs:.1f} s)"}
+    err = {"J_rel_l2": float(np.linalg.norm(d_gpu[rows] - d_ref) / np.linalg.norm(d_ref)),
+           "JT_rel_l2": float(np.linalg.norm(g_gpu[vox] - g_ref) / np.linalg.norm(g_ref)),
+           "sample": f"J on the {n_rows} oracle rows, J^T on {n_vox} random voxels"}
+    return cpu, err
 
 
 def run_reference(args, ws, rank):
@@ -238,26 +248,37 @@ def run_psf(args, ws, rank, local):
             nrm = float(fp[sb, k].double().norm())
             if nrm > 0:
                 diff.append(float((tc[sb, k].double() - fp[sb, k].double()).norm()) / nrm)
-    # FP64 oracle on sampled voxels of a few PSFs
-    import oracle
-    og = oracle.Geometry.from_workload(w)
-    rng = np.random.default_rng(12)
-    errs_tc, errs_fp = [], []
-    for k in range(min(2, k32)):
-        vk = int(spikes[k])
-        i, j, z = vk % w.grid.nx, (vk // w.grid.nx) % w.grid.ny, vk // (w.grid.nx * w.grid.ny)
-        near = []
-        for _ in range(256):
-            di, dj, dz = rng.integers(-20, 21, 3)
-            ii, jj, zz = min(max(i + di, 0), w.grid.nx - 1), min(max(j + dj, 0), w.grid.ny - 1), \
-                min(max(z + dz, 0), w.grid.nz - 1)
-            near.append((zz * w.grid.ny + jj) * w.grid.nx + ii)
-        vox = np.unique(np.array(near, dtype=np.int64))
-        for sb in (0, 2):
-            ref = og.psf(np.array([vk]), [subsets[sb]], vox)[0, 0]
-            n = np.linalg.norm(ref)
-            errs_tc.append(float(np.linalg.norm(tc[sb, k][torch.as_tensor(vox, device="cuda")].double().cpu().numpy() - ref) / n))
-            errs_fp.append(float(np.linalg.norm(fp[sb, k][torch.as_tensor(vox, device="cuda")].double().cpu().numpy() - ref) / n))
+    # CPU baseline leg: the FP64 oracle on sampled voxels of a few PSFs (timed, and the same
+    # values give the sampled error of both GPU paths)
+    errs_tc, errs_fp, cpu = [], [], None
+    if not args.no_cpu_baseline and rank == 0:
+        import oracle
+        og = oracle.Geometry.from_workload(w)
+        rng = np.random.default_rng(12)
+        secs, n_vals = 0.0, 0
+        for k in range(min(2, k32)):
+            vk = int(spikes[k])
+            i, j, z = vk % w.grid.nx, (vk // w.grid.nx) % w.grid.ny, vk // (w.grid.nx * w.grid.ny)
+            near = []
+            for _ in range(256):
+                di, dj, dz = rng.integers(-20, 21, 3)
+                ii, jj, zz = min(max(i + di, 0), w.grid.nx - 1), min(max(j + dj, 0), w.grid.ny - 1), \
+                    min(max(z + dz, 0), w.grid.nz - 1)
+                near.append((zz * w.grid.ny + jj) * w.grid.nx + ii)
+            vox = np.unique(np.array(near, dtype=np.int64))
+            for sb in (0, 2):
+                t0 = time.perf_counter()
+                ref = og.psf(np.array([vk]), [subsets[sb]], vox)[0, 0]
+                secs += time.perf_counter() - t0
+                n_vals += len(vox)
+                n = np.linalg.norm(ref)
+                vt = torch.as_tensor(vox, device="cuda")
+                errs_tc.append(float(np.linalg.norm(tc[sb, k][vt].double().cpu().numpy() - ref) / n))
+                errs_fp.append(float(np.linalg.norm(fp[sb, k][vt].double().cpu().numpy() - ref) / n))
+        cpu = {"value": 1e3 * secs / n_vals * n_psf * geo.V, "unit": "ms", "cores": oracle.n_threads(),
+               "kind": "oracle",
+               "sample": f"FP64 oracle PSF values at {n_vals} voxels (2 spikes x subsets {{64, 256}}, within 20 "
+                         f"voxels of the spike) in {secs:.1f} s, scaled linearly to {n_psf} PSFs x {geo.V} voxels"}
     fp_full_ms = fp_ms * len(spikes) / k32
     tc_avg = statistics.mean(tc_ms)
     info = geo.info()
@@ -274,7 +295,9 @@ def run_psf(args, ws, rank, local):
         "speedup_tc_vs_fp32": fp_full_ms / tc_avg,
         "tc_vs_fp32_rel_l2_max": max(diff) if diff else None,
         "err_vs_fp64_oracle": {"tc_rel_l2_max": max(errs_tc), "fp32_rel_l2_max": max(errs_fp),
-                               "sample": "2 spikes x subsets {64, 256}, <=256 voxels within 20 of the spike"},
+                               "sample": "2 spikes x subsets {64, 256}, <=256 voxels within 20 of the spike"}
+        if errs_tc else None,
+        "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -420,29 +443,14 @@ def main():
         e2e_ms.append(1e3 * (time.perf_counter() - t_a))
     e2e_total = max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws)
 
-    # ---- parity against the FP64 oracle on sampled rows and voxels (rank 0)
+    # ---- CPU baseline leg (rank 0): the FP64 oracle on sampled rows (J, timed) and voxels
+    #      (J^T); the same outputs give the sampled error of the GPU results
     err = None
     cpu = None
-    if rank == 0:
-        import oracle
-        og = oracle.Geometry.from_workload(w)
-        rng = np.random.default_rng(99)
-        rows = np.sort(rng.choice(og.M, 128, replace=False)).astype(np.int64)
-        vox = np.sort(rng.choice(og.V, 1024, replace=False)).astype(np.int64)
-        m_np = wl.model_for(w)
-        dj = geo.J(m_true).double().cpu().numpy()[rows]
-        dj_ref = og.J(m_np, rows)
-        rr = r.double().cpu().numpy()
-        gj = geo.JT(r).double().cpu().numpy()[vox]
-        gj_ref = og.JT(rr, vox)
-        err = {"J_rel_l2": float(np.linalg.norm(dj - dj_ref) / np.linalg.norm(dj_ref)),
-               "JT_rel_l2": float(np.linalg.norm(gj - gj_ref) / np.linalg.norm(gj_ref)),
-               "sample": "J on 128 random rows, J^T on 1024 random voxels"}
-        if not args.no_cpu_baseline:
-            rate, secs, units, threads = oracle_sample_rate(w, args.cpu_rows)
-            cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                   "sample": f"FP64 oracle J on {args.cpu_rows} random rows of {w.name} "
-                             f"({units} in-support evals, {secs:.1f} s)"}
+    if rank == 0 and not args.no_cpu_baseline:
+        dj = geo.J(m_true).double().cpu().numpy()
+        gj = geo.JT(r).double().cpu().numpy()
+        cpu, err = oracle_leg(w, args.cpu_rows, 1024, dj, r.double().cpu().numpy(), gj)
 
     if rank != 0:
         return 0
