@@ -475,6 +475,7 @@ def main():
         "ms_per_cg_iter": total_ms / args.steps / n_iter,
         "ms_per_J": 1e3 * j_avg, "ms_per_JT": 1e3 * jt_avg,
         "J_evals_per_s": support / j_avg, "JT_evals_per_s": support / jt_avg,
+        "J_dense_equiv_per_s": geo.M * geo.V / j_avg, "JT_dense_equiv_per_s": geo.M * geo.V / jt_avg,
         "setup_ms": {"table": 1e3 * (t1 - t0), "geometry_and_cull": 1e3 * (t2 - t1)},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
                      "frac": achieved / peak_evals, "traffic": APPLY_TRAFFIC_BYTES,

@@ -25,7 +25,7 @@ import ctypes
 import os
 import subprocess
 import threading
-from typing import Optional, Sequence
+from typing import Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -53,12 +53,16 @@ def lib():
             build()
             L = ctypes.CDLL(_LIB_PATH)
             d, i32, i64, vp = ctypes.c_double, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
-            geom = [vp, vp, vp, vp, vp, i32, i32, i32, i32, d, vp, d]
+            geom = [vp, vp, vp, vp, vp, i32, i32, i32, i32, d, vp, d, vp]
             L.oracle_phi_table.argtypes = [ctypes.c_int, d, d, vp, vp, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, d, vp]
             L.oracle_phi_table.restype = ctypes.c_int
             L.oracle_phi.argtypes = [vp, ctypes.c_int, d, d]
             L.oracle_phi.restype = d
+            L.oracle_trig_coefs.argtypes = [d, d, d, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+            L.oracle_trig_coefs.restype = ctypes.c_int
+            L.oracle_phi_trig.argtypes = [vp, ctypes.c_int, d, d, d]
+            L.oracle_phi_trig.restype = d
             L.oracle_detour.argtypes = [vp, vp, vp, vp, vp, vp, vp]
             L.oracle_detour_naive.argtypes = [vp, vp, vp]
             L.oracle_detour_naive.restype = d
@@ -120,6 +124,26 @@ def phi_lookup(table: np.ndarray, dt_max: float, dt: float) -> float:
     return lib().oracle_phi(_p(t), len(t), dt_max, float(dt))
 
 
+def trig_coefs(f_center: float, f_sigma: float, dt_max: float, n_terms: int = 0,
+               n_quad: int = 40000) -> Tuple[np.ndarray, float]:
+    """Sine-series form of Phi for the Gaussian power spectrum: (a_j for j = 1..n, dw), with
+    Phi(dt) = sum_j a_j sin(j dw dt) (n chosen by the oracle's rule unless n_terms > 0)."""
+    a = np.empty(4096)
+    dw = ctypes.c_double()
+    n = ctypes.c_int()
+    rc = lib().oracle_trig_coefs(f_center, f_sigma, dt_max, int(n_terms), n_quad, _p(a), ctypes.byref(dw),
+                                 ctypes.byref(n))
+    if rc != 0:
+        raise ValueError("oracle_trig_coefs rejected its arguments")
+    return a[:n.value].copy(), dw.value
+
+
+def phi_trig(a: np.ndarray, dw: float, dt_max: float, dt: float) -> float:
+    """The truncated sine series at one dt (FP64, term by term)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return lib().oracle_phi_trig(_p(a), len(a), float(dw), float(dt_max), float(dt))
+
+
 def detour(xs, xr, x):
     """(R, R_xs, R_xr, L) in metres by the cancellation-free form."""
     a = [np.ascontiguousarray(v, dtype=np.float64) for v in (xs, xr, x)]
@@ -145,12 +169,19 @@ class Geometry:
     """Arrays describing rows, voxels and tables, held as contiguous numpy buffers."""
 
     def __init__(self, tx: np.ndarray, rows: np.ndarray, band: Optional[np.ndarray],
-                 tables: Sequence[np.ndarray], dt_max: Sequence[float], grid, c0: float):
+                 tables: Sequence[np.ndarray], dt_max: Sequence[float], grid, c0: float,
+                 trig_dw: Optional[Sequence[float]] = None):
+        """tables: per band either a sampled Phi table (trig_dw None) or the coefficients of the
+        sine series with node spacing trig_dw[band] (bands of different lengths are zero-padded)."""
         self.tx = np.ascontiguousarray(tx, dtype=np.float64)
         self.rows = np.ascontiguousarray(rows, dtype=np.int32)
         self.M = int(self.rows.shape[0])
         self.band = None if band is None else np.ascontiguousarray(band, dtype=np.int32)
-        self.tables = np.ascontiguousarray(np.stack(tables), dtype=np.float64)
+        n = max(len(t) for t in tables)
+        self.tables = np.zeros((len(tables), n))
+        for b, t in enumerate(tables):
+            self.tables[b, :len(t)] = t
+        self.trig_dw = None if trig_dw is None else np.ascontiguousarray(trig_dw, dtype=np.float64)
         self.dt_max = np.ascontiguousarray(dt_max, dtype=np.float64)
         self.grid = grid
         self.org = np.ascontiguousarray(grid.origin, dtype=np.float64)
@@ -158,7 +189,13 @@ class Geometry:
         self.V = grid.n_vox
 
     @staticmethod
-    def from_workload(w, tables: Optional[Sequence[np.ndarray]] = None) -> "Geometry":
+    def from_workload(w, tables: Optional[Sequence[np.ndarray]] = None, phi: str = "table",
+                      n_terms: int = 0) -> "Geometry":
+        """phi = "table" (sampled, linear interpolation) or "trig" (sine series)."""
+        if phi == "trig":
+            series = [trig_coefs(b.f_center_hz, b.f_sigma_hz, b.dt_max, n_terms) for b in w.bands]
+            return Geometry(w.tx, w.row_pairs(), w.band_of_row, [a for a, _ in series],
+                            [b.dt_max for b in w.bands], w.grid, w.c0, trig_dw=[dw for _, dw in series])
         if tables is None:
             tables = [phi_table_gauss(b.f_center_hz, b.f_sigma_hz, b.n_samples, b.dt_max) for b in w.bands]
         return Geometry(w.tx, w.row_pairs(), w.band_of_row, tables, [b.dt_max for b in w.bands],
@@ -167,7 +204,7 @@ class Geometry:
     def _args(self):
         g = self.grid
         return (_p(self.tx), _p(self.rows), _p(self.band), _p(self.tables), _p(self.dt_max),
-                int(self.tables.shape[1]), g.nx, g.ny, g.nz, g.h, _p(self.org), self.c0)
+                int(self.tables.shape[1]), g.nx, g.ny, g.nz, g.h, _p(self.org), self.c0, _p(self.trig_dw))
 
     def entry(self, p: int, v: int) -> float:
         return lib().oracle_J_entry(*self._args(), int(p), int(v))

@@ -18,6 +18,10 @@
  *                  upper limits read as infinity; sampled at dt_k = k dt_max / (n-1).
  *   phi lookup     Sec. II-C: the operator is truncated at a maximum detour; Phi = 0 for
  *                  dt >= dt_max and for dt <= 0, linear interpolation in between.
+ *   phi series     Sec. II-C: the alternative the paper stores, the coefficients and
+ *                  arguments of the sine terms of Eq. Kernel_freq: both frequency integrals
+ *                  by a rectangle rule on equally spaced nodes, Phi = sum_j a_j sin(w_j dt),
+ *                  summed term by term in FP64, same truncation.
  *   detour         Sec. II-C: R = R_xs + R_xr - R_sr, dt = R / c0, evaluated in a form
  *                  with only non-negative terms (no cancellation near the ray).
  *   K0             Eq. Kernel_freq with A from Eq. Linearized_sensitivity:
@@ -131,6 +135,52 @@ int oracle_phi_table(int kind, double fc, double fsig, const double* om, const d
     return -1;
 }
 
+/*
+ * Sine-series form of Phi (Sec. II-C, Eq. Kernel_freq), Gaussian spectrum.
+ * Nodes w_j = j dw, j = 1..n; with the rectangle rule for both integrals
+ *   Phi(dt) = sum_j a_j sin(w_j dt),   a_j = dw w_j^3 W(w_j) / int_0^inf w^2 W(w) dw,
+ * the denominator by the composite Simpson rule of oracle_phi_table (n_quad intervals).
+ * The rule is exact up to aliasing from the period T = 2 pi / dw of the series and the
+ * truncation of the terms (reading of the paper's "very few terms"):
+ *   T = max(2 dt_max, dt_max + 6.5 / s)   (Phi decays like exp(-s^2 t^2 / 2): images of
+ *                                          Phi shifted by T are negligible on [0, dt_max]),
+ *   n = ceil((w0 + 6.5 s) / dw)           (W < 1e-9 beyond), unless n_terms > 0 is given.
+ * a must hold n values (at most 4096). Returns 0, or -1 on bad arguments.
+ */
+int oracle_trig_coefs(double fc, double fsig, double dt_max, int n_terms, int n_quad, double* a,
+                      double* dw_out, int* n_out) {
+    if (!(fc > 0) || !(fsig > 0) || !(dt_max > 0) || n_quad < 2 || (n_quad & 1) || !a) return -1;
+    double w0 = 2 * ORC_PI * fc, s = 2 * ORC_PI * fsig;
+    double T = 2.0 * dt_max;
+    if (dt_max + 6.5 / s > T) T = dt_max + 6.5 / s;
+    double dw = 2 * ORC_PI / T;
+    int n = n_terms > 0 ? n_terms : (int)ceil((w0 + 6.5 * s) / dw);
+    if (n < 1 || n > 4096) return -1;
+    double wmax = w0 + 12 * s, hq = wmax / n_quad;
+    ksum den = {0, 0};
+    for (int q = 0; q <= n_quad; ++q) {
+        double w = q * hq;
+        double c = (q == 0 || q == n_quad) ? 1.0 : ((q & 1) ? 4.0 : 2.0);
+        kadd(&den, c * w * w * w_gauss(w, w0, s));
+    }
+    double D = den.s * hq / 3.0;
+    for (int j = 1; j <= n; ++j) {
+        double w = j * dw;
+        a[j - 1] = dw * w * w * w * w_gauss(w, w0, s) / D;
+    }
+    if (dw_out) *dw_out = dw;
+    if (n_out) *n_out = n;
+    return 0;
+}
+
+/* The truncated series: 0 for dt <= 0 or dt >= dt_max, else sum_j a_j sin(j dw dt). */
+double oracle_phi_trig(const double* a, int n, double dw, double dt_max, double dt) {
+    if (!(dt > 0.0) || dt >= dt_max) return 0.0;
+    ksum acc = {0, 0};
+    for (int j = 1; j <= n; ++j) kadd(&acc, a[j - 1] * sin(j * dw * dt));
+    return acc.s;
+}
+
 /* Truncated, linearly interpolated Phi (Sec. II-C truncation). */
 double oracle_phi(const double* tab, int n, double dt_max, double dt) {
     if (!(dt > 0.0) || dt >= dt_max) return 0.0;
@@ -215,6 +265,8 @@ typedef struct {
     double h;
     double org[3];
     double c0;
+    const double* trig_dw;   /* n_bands, nullable: NULL = sampled tables; else tables hold the
+                                n_tab sine-series coefficients of each band, node spacing dw */
 } orc_geom;
 
 static void vox_centre(const orc_geom* g, int64_t v, double* x) {
@@ -254,15 +306,22 @@ static inline double jentry(const orc_geom* g, int64_t p, const double* x) {
     const double* xs = g->tx + 3 * (int64_t)g->rows[2 * p];
     const double* xr = g->tx + 3 * (int64_t)g->rows[2 * p + 1];
     int b = g->band ? g->band[p] : 0;
-    return oracle_k0(xs, xr, x, g->c0, g->tables + (int64_t)b * g->n_tab, g->n_tab, g->dt_max[b]) *
-           g->h * g->h * g->h;
+    const double* tab = g->tables + (int64_t)b * g->n_tab;
+    if (g->trig_dw) {   /* K0 with the sine-series Phi */
+        double R, rs, rr, L;
+        oracle_detour(xs, xr, x, &R, &rs, &rr, &L);
+        if (rs == 0.0 || rr == 0.0) return 0.0;
+        double phi = oracle_phi_trig(tab, g->n_tab, g->trig_dw[b], g->dt_max[b], R / g->c0);
+        return -L / (2.0 * ORC_PI * g->c0 * g->c0 * g->c0 * (rs * rr)) * phi * g->h * g->h * g->h;
+    }
+    return oracle_k0(xs, xr, x, g->c0, tab, g->n_tab, g->dt_max[b]) * g->h * g->h * g->h;
 }
 
 #define GEOM_ARGS const double *tx, const int32_t *rows, const int32_t *band, \
     const double *tables, const double *dt_max, int32_t n_tab, int32_t nx, int32_t ny, \
-    int32_t nz, double h, const double *org, double c0
+    int32_t nz, double h, const double *org, double c0, const double *trig_dw
 #define GEOM_INIT orc_geom G = {tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, \
-    {org[0], org[1], org[2]}, c0}; const orc_geom* g = &G
+    {org[0], org[1], org[2]}, c0, trig_dw}; const orc_geom* g = &G
 
 /* J entry for (row p, voxel v). */
 double oracle_J_entry(GEOM_ARGS, int64_t p, int64_t v) {
@@ -400,20 +459,20 @@ int oracle_cgls(GEOM_ARGS, int64_t M, const double* dobs, double lambda, int32_t
     double* s = (double*)malloc(sizeof(double) * (size_t)V);
     double* p = (double*)malloc(sizeof(double) * (size_t)V);
     int status = 0;
-    oracle_J(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, M, NULL, 0, m, r);
+    oracle_J(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, trig_dw, M, NULL, 0, m, r);
     for (int64_t i = 0; i < M; ++i) r[i] = dobs[i] - r[i];
-    oracle_JT(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, M, r, NULL, 0, s);
+    oracle_JT(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, trig_dw, M, r, NULL, 0, s);
     for (int64_t v = 0; v < V; ++v) { s[v] -= lambda * m[v]; p[v] = s[v]; }
     double gamma = dot(s, s, V);
     if (hist) hist[0] = gamma;
     for (int32_t it = 0; it < n_iter; ++it) {
-        oracle_J(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, M, NULL, 0, p, q);
+        oracle_J(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, trig_dw, M, NULL, 0, p, q);
         double delta = dot(q, q, M) + lambda * dot(p, p, V);
         if (!(delta > 0.0) || !isfinite(gamma)) { status = -4; break; }
         double alpha = gamma / delta;
         for (int64_t v = 0; v < V; ++v) m[v] += alpha * p[v];
         for (int64_t i = 0; i < M; ++i) r[i] -= alpha * q[i];
-        oracle_JT(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, M, r, NULL, 0, s);
+        oracle_JT(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, trig_dw, M, r, NULL, 0, s);
         for (int64_t v = 0; v < V; ++v) s[v] -= lambda * m[v];
         double gnew = dot(s, s, V);
         double beta = gnew / gamma;
@@ -448,7 +507,7 @@ void oracle_psf(GEOM_ARGS, int64_t M, const int64_t* spikes, int32_t n_spike,
                 dcol[p] = jentry(g, p, xk);
             }
             double* o = out + ((int64_t)sb * n_spike + k) * nv;
-            oracle_JT(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, M, dcol,
+            oracle_JT(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, trig_dw, M, dcol,
                       vox_idx, nv, o);
         }
     }
