@@ -141,12 +141,13 @@ def max_over_ranks(x: float, ws: int) -> float:
 
 # --------------------------------------------------------------------------- CPU oracle legs
 
-def oracle_leg(w, n_rows: int, n_vox: int, d_gpu, r_host, g_gpu, seed: int = 0):
+def oracle_leg(w, n_rows: int, n_vox: int, d_gpu, r_host, g_gpu, seed: int = 0, phi: str = "table",
+               trig_terms: int = 0):
     """The FP64 oracle on a bounded sample of the workload: J on n_rows random rows (timed:
     in-support evals/s on the host cores) and J^T on n_vox random voxels. Returns the
     cpu_baseline record and the relative L2 errors of the GPU's J and J^T on the sample."""
     import oracle
-    og = oracle.Geometry.from_workload(w)
+    og = oracle.Geometry.from_workload(w, phi=phi, n_terms=trig_terms)
     rng = np.random.default_rng(seed)
     rows = np.sort(rng.choice(og.M, n_rows, replace=False)).astype(np.int64)
     vox = np.sort(rng.choice(og.V, n_vox, replace=False)).astype(np.int64)
@@ -321,6 +322,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=1024)
     ap.add_argument("--cpu-rows", type=int, default=4096)
+    ap.add_argument("--phi", default="table", choices=["table", "trig"],
+                    help="Phi representation: sampled table (default) or sine series")
+    ap.add_argument("--trig-terms", type=int, default=0, help="sine-series terms (0: automatic)")
     ap.add_argument("--mode", default="solve", choices=["solve", "apply"],
                     help="apply: only build the geometry and run --steps J^T and J applications "
                          "(a short program for ncu captures; prints timings, not the bench line)")
@@ -342,7 +346,10 @@ def main():
     # ---- setup (not part of a step): tables, geometry, data
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tables = [fg.Table(b.f_center_hz, b.f_sigma_hz, b.n_samples, b.dt_max) for b in w.bands]
+    if args.phi == "trig":
+        tables = [fg.TrigTable(b.f_center_hz, b.f_sigma_hz, b.dt_max, args.trig_terms) for b in w.bands]
+    else:
+        tables = [fg.Table(b.f_center_hz, b.f_sigma_hz, b.n_samples, b.dt_max) for b in w.bands]
     t1 = time.perf_counter()
     geo = fg.Geometry(w.tx, w.row_pairs(), w.grid, w.c0, tables,
                       band_of_row=w.band_of_row if len(w.bands) > 1 else None, dt_mode=args.dt_mode)
@@ -450,7 +457,8 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         dj = geo.J(m_true).double().cpu().numpy()
         gj = geo.JT(r).double().cpu().numpy()
-        cpu, err = oracle_leg(w, args.cpu_rows, 1024, dj, r.double().cpu().numpy(), gj)
+        cpu, err = oracle_leg(w, args.cpu_rows, 1024, dj, r.double().cpu().numpy(), gj, phi=args.phi,
+                              trig_terms=args.trig_terms)
 
     if rank != 0:
         return 0
@@ -458,7 +466,11 @@ def main():
     props = torch.cuda.get_device_properties(dev)
     sm_count = props.multi_processor_count
     sm_max = float(pk.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
-    peak_evals = sm_count * FP32_LANES_PER_SM_CLK * sm_max * 1e6 / OPS_PER_EVAL
+    # canonical FP32 operations per evaluation: the 24-op table mix; with the sine series the
+    # 4-op lookup becomes 16 ops (sin, cos, argument, cut) plus 2 per term of the recurrence
+    n_terms = int(info.phi_terms)
+    ops = OPS_PER_EVAL if n_terms == 0 else OPS_PER_EVAL - 4 + 16 + 2 * n_terms
+    peak_evals = sm_count * FP32_LANES_PER_SM_CLK * sm_max * 1e6 / ops
     jt_avg = statistics.mean(jt_ms) * 1e-3
     j_avg = statistics.mean(j_ms) * 1e-3
     achieved = support / jt_avg
@@ -471,6 +483,7 @@ def main():
         "config": {"workload": w.name, "pairs": geo.M, "voxels": geo.V, "cg_iters": n_iter,
                    "support_evals_per_apply": support, "evaluated_evals_per_apply": int(info.evaluated_evals),
                    "dt_mode": ["stable", "naive", "fp64"][args.dt_mode],
+                   "phi": "table (4096 samples)" if n_terms == 0 else f"sine series ({n_terms} terms)",
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{ws}"},
         "ms_per_cg_iter": total_ms / args.steps / n_iter,
         "ms_per_J": 1e3 * j_avg, "ms_per_JT": 1e3 * jt_avg,
@@ -481,7 +494,7 @@ def main():
                      "frac": achieved / peak_evals, "traffic": APPLY_TRAFFIC_BYTES,
                      "kernel": "apply_kernel (J^T) + jt_reduce",
                      "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM_CLK} FP32 lanes x {sm_max:.0f} MHz "
-                                   f"({pk_kind}) / {OPS_PER_EVAL} ops per eval"},
+                                   f"({pk_kind}) / {ops} ops per eval"},
         "err_vs_fp64_oracle": err,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * evals_per_step / (e2e_total * 1e-3), "unit": UNIT,

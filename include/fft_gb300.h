@@ -72,7 +72,7 @@ typedef struct {
     double origin[3];
 } fft_grid;
 
-typedef struct fft_table_s* fft_table; /* opaque: one sampled Phi table */
+typedef struct fft_table_s* fft_table; /* opaque: one Phi representation (sampled table or sine series) */
 typedef struct fft_geom_s* fft_geom;   /* opaque: rows + grid + tables + cull lists */
 
 /*
@@ -93,6 +93,30 @@ fft_status fft_table_build(const fft_spectrum* spec, int32_t n_samples, double d
 void fft_table_destroy(fft_table t);
 
 /*
+ * fft_trig_build - Phi as a short sine series, the form Sec. II-C stores ("coefficients and
+ * arguments" of the trigonometric terms of Eq. Kernel_freq) in place of a sampled table:
+ *   Phi(dt) = sum_{j=1..n} a_j sin(j dw dt),  0 for dt <= 0 or dt >= dt_max,
+ *   a_j = dw w_j^3 W(w_j) / int_0^inf w^2 W(w) dw,  w_j = j dw,
+ * i.e. both integrals by the rectangle rule on equally spaced nodes (the denominator in
+ * closed form for the Gaussian W). Node spacing dw = 2 pi / T with the period
+ * T = max(2 dt_max, dt_max + 6.5 / s): shifted images of Phi (which decays like
+ * exp(-s^2 t^2 / 2)) are then negligible on [0, dt_max], and x = dw dt stays in [0, pi].
+ *   spec         Gaussian spectrum only (kind 0); kind 1 gives FFT_ERR_ARG.
+ *   dt_max       cut-off detour time in s (> 0).
+ *   n_terms      0: automatic, n = ceil((w0 + 5.5 s) / dw) (W < 3e-7 beyond, series within 2e-8
+ *                of max |Phi|; 18..20 terms for the reference workloads); else 1 .. 256 terms.
+ *   coef_out     nullable, host: receives the n FP64 coefficients a_1 .. a_n.
+ *   dw_out       nullable, host: receives dw (rad/s).
+ *   n_terms_out  nullable, host: receives n.
+ *   out          receives the handle; release with fft_table_destroy.
+ * Geometries built from series handles evaluate Phi on the fly by the Clenshaw recurrence
+ * (one sine and one cosine per evaluation, two FP32 operations per term) instead of the
+ * table lookup. Synchronous; host-only arithmetic.
+ */
+fft_status fft_trig_build(const fft_spectrum* spec, double dt_max, int32_t n_terms, double* coef_out,
+                          double* dw_out, int32_t* n_terms_out, fft_table* out);
+
+/*
  * fft_geom_create - set up the operator J for one acquisition (Eq. forward_compact):
  *   tx_xyz       host, n_tx x 3 transducer positions (m).
  *   rows         host, n_rows x 2 (s, r) transducer indices, s != r. Row order is the
@@ -111,6 +135,9 @@ fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const int32_t* ro
                            int64_t n_rows, const int32_t* band_of_row, const fft_grid* grid,
                            double c0, const fft_table* tables, int32_t n_tables,
                            int32_t dt_mode, fft_geom* out);
+/* (fft_geom_create, continued) tables must all be sampled tables (fft_table_build) or all sine
+ * series (fft_trig_build); a series geometry needs dt_mode FFT_DT_STABLE and supports J, J^T,
+ * the Frobenius norm and CG; fft_psf_batch and fft_psf_noalloc reject it (FFT_ERR_ARG). */
 void fft_geom_destroy(fft_geom g);
 
 /* Sizes and counters of a geometry (host struct filled synchronously). */
@@ -124,6 +151,7 @@ typedef struct {
     int64_t scratch_bytes;   /* device bytes owned by the handle */
     int32_t dt_mode;
     int64_t evaluated_evals; /* (row, voxel) evaluations one apply performs after culling */
+    int32_t phi_terms;       /* 0: sampled tables; else the largest sine-series length */
 } fft_geom_info_t;
 fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info);
 

@@ -144,7 +144,8 @@ int oracle_phi_table(int kind, double fc, double fsig, const double* om, const d
  * truncation of the terms (reading of the paper's "very few terms"):
  *   T = max(2 dt_max, dt_max + 6.5 / s)   (Phi decays like exp(-s^2 t^2 / 2): images of
  *                                          Phi shifted by T are negligible on [0, dt_max]),
- *   n = ceil((w0 + 6.5 s) / dw)           (W < 1e-9 beyond), unless n_terms > 0 is given.
+ *   n = ceil((w0 + 5.5 s) / dw)           (W < 3e-7 beyond; series error < 2e-8 of max |Phi|),
+ *                                          unless n_terms > 0 is given.
  * a must hold n values (at most 4096). Returns 0, or -1 on bad arguments.
  */
 int oracle_trig_coefs(double fc, double fsig, double dt_max, int n_terms, int n_quad, double* a,
@@ -154,7 +155,7 @@ int oracle_trig_coefs(double fc, double fsig, double dt_max, int n_terms, int n_
     double T = 2.0 * dt_max;
     if (dt_max + 6.5 / s > T) T = dt_max + 6.5 / s;
     double dw = 2 * ORC_PI / T;
-    int n = n_terms > 0 ? n_terms : (int)ceil((w0 + 6.5 * s) / dw);
+    int n = n_terms > 0 ? n_terms : (int)ceil((w0 + 5.5 * s) / dw);
     if (n < 1 || n > 4096) return -1;
     double wmax = w0 + 12 * s, hq = wmax / n_quad;
     ksum den = {0, 0};

@@ -25,8 +25,8 @@ from ._lib import (FFT_DT_FP64, FFT_DT_NAIVE, FFT_DT_STABLE, FFTError, check, ff
                    fft_grid, fft_spectrum)
 
 __all__ = [
-    "Table", "Geometry", "JFunction", "jacobian_apply", "FFTError",
-    "fft_table_build", "fft_geom_create", "fft_J_apply", "fft_JT_apply", "fft_cg_solve", "fft_psf_batch",
+    "Table", "TrigTable", "Geometry", "JFunction", "jacobian_apply", "FFTError",
+    "fft_table_build", "fft_trig_build", "fft_geom_create", "fft_J_apply", "fft_JT_apply", "fft_cg_solve", "fft_psf_batch",
     "FFT_DT_STABLE", "FFT_DT_NAIVE", "FFT_DT_FP64", "fresnel_width", "build",
 ]
 
@@ -104,6 +104,32 @@ class Table:
             self.close()
         except Exception:
             pass
+
+
+class TrigTable(Table):
+    """Phi as a short sine series (the form Sec. II-C stores): Phi(dt) = sum_j a_j sin(j dw dt)
+    for a Gaussian power spectrum; ``n_terms`` 0 picks the count automatically. ``coef``,
+    ``dw`` and ``n`` are the series the library built (host copies)."""
+
+    def __init__(self, f_center: float, f_sigma: float, dt_max: Optional[float] = None, n_terms: int = 0):
+        L = _lib.load()
+        spec = fft_spectrum()
+        spec.kind, spec.f_center_hz, spec.f_sigma_hz = 0, float(f_center), float(f_sigma)
+        spec.omega = spec.weight = None
+        spec.n_omega = 0
+        self._keep = []
+        self.dt_max = float(3.0 / float(f_center) if dt_max is None else dt_max)
+        coef = np.empty(256)
+        dw = ctypes.c_double()
+        n = ctypes.c_int32()
+        h = ctypes.c_void_p()
+        check(L.fft_trig_build(ctypes.byref(spec), self.dt_max, int(n_terms), coef.ctypes.data,
+                               ctypes.byref(dw), ctypes.byref(n), ctypes.byref(h)))
+        self.handle = h
+        self.n = int(n.value)
+        self.dw = float(dw.value)
+        self.coef = coef[:self.n].copy()
+        self.host = None
 
 
 def fft_table_build(f_center=None, f_sigma=None, n=4096, dt_max=None, omega=None, weight=None,
@@ -218,6 +244,10 @@ class Geometry:
             self.close()
         except Exception:
             pass
+
+
+def fft_trig_build(f_center, f_sigma, dt_max=None, n_terms=0) -> TrigTable:
+    return TrigTable(f_center, f_sigma, dt_max, n_terms)
 
 
 def fft_geom_create(tx, rows, grid, c0, tables, band_of_row=None, dt_mode=FFT_DT_STABLE) -> Geometry:

@@ -55,7 +55,7 @@ class fft_geom_info_t(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("n_vox", ctypes.c_int64), ("n_entries", ctypes.c_int64),
                 ("n_items", ctypes.c_int64), ("support_evals", ctypes.c_int64),
                 ("scratch_bytes", ctypes.c_int64), ("dt_mode", ctypes.c_int32),
-                ("evaluated_evals", ctypes.c_int64)]
+                ("evaluated_evals", ctypes.c_int64), ("phi_terms", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) for every function declared in include/fft_gb300.h
@@ -63,6 +63,7 @@ _VP, _I32, _I64, _D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_
 SIGNATURES = {
     "fft_table_build": (ctypes.c_int, [ctypes.POINTER(fft_spectrum), _I32, _D, _VP, ctypes.POINTER(_VP)]),
     "fft_table_destroy": (None, [_VP]),
+    "fft_trig_build": (ctypes.c_int, [ctypes.POINTER(fft_spectrum), _D, _I32, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
     "fft_geom_create": (ctypes.c_int, [_VP, _I32, _VP, _I64, _VP, ctypes.POINTER(fft_grid), _D, _VP, _I32,
                                        _I32, ctypes.POINTER(_VP)]),
     "fft_geom_destroy": (None, [_VP]),

@@ -51,7 +51,16 @@ struct ApplyParams {
     float* gpart;            // J^T partials of multi-item tiles
     double* dsum;            // FROB: [n_items * 8]
     unsigned long long* icount;   // COUNT
+    int trig_nq;             // sine-series Phi: coefficient groups of 4 per band
 };
+
+// Phi of the normalised detour v from the band data at shared address tb (table lookup or
+// sine series, see fft_device.cuh).
+template <int PHI>
+__device__ __forceinline__ float phi_eval(float v, uint32_t tb, float nm1, int nq) {
+    if (PHI == PHI_TRIG) return phi_trig(v, tb, nq);
+    return phi_lookup(v, tb, nm1);
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -90,7 +99,7 @@ __device__ __forceinline__ float detour_v64(const RowRec64& r, double ox, double
     return (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
 }
 
-template <int MODE, int DT, bool GUARD, bool SHARP>
+template <int MODE, int DT, bool GUARD, bool SHARP, int PHI>
 __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(const __grid_constant__ ApplyParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* s_tab = reinterpret_cast<float2*>(smem);
@@ -103,6 +112,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
 
     const uint32_t tab_addr = smem_addr(s_tab);
     const float nm1 = (float)(P.n_tab - 1);
+    const int nq = P.trig_nq;
     const int lx = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
     float4* stg = s_stage + warp * 96;
     const int n_units = P.n_items * APPLY_WARPS;
@@ -185,7 +195,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                 const float pcx = fmaf(cx, ex, cz * ez);
                 in0 = fabsf(fmaf(cy0, ey, pcx)) + pext <= hl;
                 in1 = fabsf(fmaf(cy1, ey, pcx)) + pext <= hl;
-                const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8;
+                const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - (PHI == PHI_TABLE ? MAGIC_BITS_X8 : 0u);
                 stg[lane * 3 + 0] = base;
                 stg[lane * 3 + 1] = make_float4(hb * ex, hb * ey, hb * ez, base3);
                 // planar pair (both transducers at one z): stepping along x changes only c3
@@ -234,6 +244,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                     const float c1sq = c1 * c1;
                     const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
 #define FFT_EVAL_SUB(INNER_V, PLANAR_V)                                                              \
+    float vv[NX_LANE], ww[NX_LANE];                                                                \
     _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                          \
         const float ft = (float)t;                                                                 \
         float is, ir, v, w;                                                                        \
@@ -270,11 +281,28 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
             }                                                                                      \
             continue;                                                                              \
         }                                                                                          \
+        if constexpr (PHI == PHI_TRIG) {                                                           \
+            vv[t] = v;                                                                             \
+            ww[t] = is * ir;                                                                       \
+            continue;                                                                              \
+        }                                                                                          \
         const float val = phi_lookup(v, tb, nm1) * (is * ir);                                      \
         if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                                  \
         if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                      \
         if (MODE == MODE_FROB) {                                                                   \
             if ((vmask >> (4 * s + t)) & 1u) part = fmaf(val, val, part);                          \
+        }                                                                                          \
+    }                                                                                              \
+    if constexpr (PHI == PHI_TRIG && MODE != MODE_COUNT) {                                         \
+        float ph[NX_LANE];                                                                         \
+        phi_trig_n<NX_LANE>(vv, tb, nq, ph);                                                       \
+        _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                      \
+            const float val = ph[t] * ww[t];                                                       \
+            if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                              \
+            if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                  \
+            if (MODE == MODE_FROB) {                                                               \
+                if ((vmask >> (4 * s + t)) & 1u) part = fmaf(val, val, part);                      \
+            }                                                                                      \
         }                                                                                          \
     }
                     const float c12sq = fmaf(c2, c2, c1sq);
@@ -339,8 +367,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                                 continue;
                             }
                             const float w = is * ir;
-                            const float val1 = phi_lookup(v, tb, nm1) * w;
-                            const float val2 = phi_lookup(v2, tb, nm1) * w;
+                            const float val1 = phi_eval<PHI>(v, tb, nm1, nq) * w;
+                            const float val2 = phi_eval<PHI>(v2, tb, nm1, nq) * w;
                             if (MODE == MODE_JT) acc[s][t] = fmaf(val2 - val1, W, acc[s][t]);
                             if (MODE == MODE_J) part = fmaf(val2 - val1, mv[s][t], part);
                             if (MODE == MODE_FROB) {
@@ -455,6 +483,7 @@ static ApplyParams make_params(fft_geom g) {
     P.gpart = g->gpart;
     P.dsum = nullptr;
     P.icount = nullptr;
+    P.trig_nq = g->trig_nq;
     return P;
 }
 
@@ -463,28 +492,29 @@ size_t apply_smem(fft_geom g) {
     return tab + (size_t)APPLY_WARPS * 96 * sizeof(float4);
 }
 
-template <int MODE, int DT, bool G, bool S>
+template <int MODE, int DT, bool G, bool S, int PHI>
 static fft_status set_attr_one(size_t smem) {
-    FFT_CUDA(cudaFuncSetAttribute(apply_kernel<MODE, DT, G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FFT_CUDA(cudaFuncSetAttribute(apply_kernel<MODE, DT, G, S, PHI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     return FFT_OK;
 }
 
-template <int MODE, int DT>
+template <int MODE, int DT, int PHI>
 static fft_status set_attr_dt(size_t smem) {
     fft_status rc;
-    if ((rc = set_attr_one<MODE, DT, false, false>(smem)) != FFT_OK) return rc;
-    if ((rc = set_attr_one<MODE, DT, true, false>(smem)) != FFT_OK) return rc;
-    if ((rc = set_attr_one<MODE, DT, false, true>(smem)) != FFT_OK) return rc;
-    return set_attr_one<MODE, DT, true, true>(smem);
+    if ((rc = set_attr_one<MODE, DT, false, false, PHI>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_one<MODE, DT, true, false, PHI>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_one<MODE, DT, false, true, PHI>(smem)) != FFT_OK) return rc;
+    return set_attr_one<MODE, DT, true, true, PHI>(smem);
 }
 
 template <int MODE>
 static fft_status set_attr_mode(size_t smem) {
     fft_status rc;
-    if ((rc = set_attr_dt<MODE, FFT_DT_STABLE>(smem)) != FFT_OK) return rc;
-    if ((rc = set_attr_dt<MODE, FFT_DT_NAIVE>(smem)) != FFT_OK) return rc;
-    return set_attr_one<MODE, FFT_DT_FP64, false, false>(smem);
+    if ((rc = set_attr_dt<MODE, FFT_DT_STABLE, PHI_TABLE>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_dt<MODE, FFT_DT_NAIVE, PHI_TABLE>(smem)) != FFT_OK) return rc;
+    if (MODE != MODE_COUNT && (rc = set_attr_dt<MODE, FFT_DT_STABLE, PHI_TRIG>(smem)) != FFT_OK) return rc;
+    return set_attr_one<MODE, FFT_DT_FP64, false, false, PHI_TABLE>(smem);
 }
 
 // Raise the dynamic shared-memory limit of every kernel instantiation once per geometry
@@ -503,7 +533,7 @@ int apply_occupancy(fft_geom g) {
     int per_sm = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<MODE_JT, FFT_DT_STABLE, false, false>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_kernel<MODE_JT, FFT_DT_STABLE, false, false, PHI_TABLE>,
                                                   APPLY_THREADS, apply_smem(g));
     if (per_sm < 1) per_sm = 1;
     if (sms < 1) sms = 1;
@@ -516,23 +546,27 @@ static fft_status launch_mode(fft_geom g, const ApplyParams& P, cudaStream_t st)
     const int ctas = g->apply_ctas;
     FFT_CUDA(cudaMemsetAsync(g->counter, 0, sizeof(int32_t), st));
     if (g->n_items == 0) return FFT_OK;
-#define FFT_LAUNCH(DTV, GV, SV) apply_kernel<MODE, DTV, GV, SV><<<ctas, APPLY_THREADS, smem, st>>>(P)
-#define FFT_LAUNCH_GS(DTV)                                          \
+    // MODE_COUNT evaluates no Phi: the table variant serves both representations
+    constexpr int PHI_T = MODE == MODE_COUNT ? PHI_TABLE : PHI_TRIG;
+#define FFT_LAUNCH(DTV, GV, SV, PV) apply_kernel<MODE, DTV, GV, SV, PV><<<ctas, APPLY_THREADS, smem, st>>>(P)
+#define FFT_LAUNCH_GS(DTV, PV)                                      \
     do {                                                            \
         if (g->guard) {                                             \
-            if (g->sharp) FFT_LAUNCH(DTV, true, true);              \
-            else FFT_LAUNCH(DTV, true, false);                      \
+            if (g->sharp) FFT_LAUNCH(DTV, true, true, PV);          \
+            else FFT_LAUNCH(DTV, true, false, PV);                  \
         } else {                                                    \
-            if (g->sharp) FFT_LAUNCH(DTV, false, true);             \
-            else FFT_LAUNCH(DTV, false, false);                     \
+            if (g->sharp) FFT_LAUNCH(DTV, false, true, PV);         \
+            else FFT_LAUNCH(DTV, false, false, PV);                 \
         }                                                           \
     } while (0)
-    if (g->dt_mode == FFT_DT_STABLE) {
-        FFT_LAUNCH_GS(FFT_DT_STABLE);
+    if (g->phi_kind == PHI_TRIG) {   // geometry creation guarantees dt_mode STABLE
+        FFT_LAUNCH_GS(FFT_DT_STABLE, PHI_T);
+    } else if (g->dt_mode == FFT_DT_STABLE) {
+        FFT_LAUNCH_GS(FFT_DT_STABLE, PHI_TABLE);
     } else if (g->dt_mode == FFT_DT_NAIVE) {
-        FFT_LAUNCH_GS(FFT_DT_NAIVE);
+        FFT_LAUNCH_GS(FFT_DT_NAIVE, PHI_TABLE);
     } else {
-        FFT_LAUNCH(FFT_DT_FP64, false, false);
+        FFT_LAUNCH(FFT_DT_FP64, false, false, PHI_TABLE);
     }
 #undef FFT_LAUNCH_GS
 #undef FFT_LAUNCH

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "fft_gb300.h"
 
@@ -68,6 +69,11 @@ struct BandConst {
 // good to ~5e-7 (FP64-derived entry bases, approximate rsqrt / rcp), so 2e-6 keeps a 4x margin.
 constexpr float CUT_BAND = 2e-6f;
 
+// Representation of Phi inside the kernels.
+enum { PHI_TABLE = 0,   // sampled table, linear interpolation (fft_table_build)
+       PHI_TRIG = 1 };  // sine series, Clenshaw recurrence (fft_trig_build)
+constexpr int TRIG_MAX_TERMS = 256;
+
 // Work item: rows [e0, e1) of tile `tile`'s entry list; J^T writes to slot `slot` of the
 // partial buffer when the tile has several items, else (slot < 0) straight to g.
 struct Item {
@@ -81,9 +87,12 @@ struct Item {
 // ------------------------------------------------------------------ handles
 struct fft_table_s {
     int dev;
-    int32_t n;
+    int32_t n;                 // samples (table) or terms (series)
     double dt_max;
-    double* d_phi;   // device FP64 samples [n]
+    double* d_phi;             // table: device FP64 samples [n]; series: nullptr
+    int32_t kind = 0;          // fftgb::PHI_TABLE or fftgb::PHI_TRIG
+    double dw = 0.0;           // series: node spacing (rad/s)
+    std::vector<double> coef;  // series: a_1 .. a_n (host, FP64)
 };
 
 struct fft_geom_s {
@@ -96,6 +105,9 @@ struct fft_geom_s {
     int32_t n_bands;
     int32_t n_tab;
     int32_t dt_mode;
+    int32_t phi_kind = 0;                // fftgb::PHI_TABLE or fftgb::PHI_TRIG (all bands alike)
+    int32_t trig_nq = 0;                 // series: coefficient groups of 4 per band (padded)
+    int32_t trig_terms = 0;              // series: the largest term count over the bands
     bool guard;                          // a (virtual) voxel centre coincides with a transducer
     bool sharp = false;                  // some band's Phi does not vanish at its cut-off
     fftgb::BandConst band[fftgb::MAX_BANDS];

@@ -30,6 +30,18 @@ __device__ __forceinline__ float2 lds_f2(uint32_t addr) {
     return v;
 }
 
+__device__ __forceinline__ float lds_f1(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ float4 lds_f4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -133,6 +145,93 @@ __device__ __forceinline__ float phi_lookup(float v, uint32_t tb, float nm1) {
     const float tt = __fmaf_rd(v, nm1, MAGIC);
     const float2 T = lds_f2(tb + (__float_as_uint(tt) << 3));
     return fmaf(v, T.y, T.x);
+}
+
+// Phi(v) from the band's sine series (Sec. II-C stored form): Phi = sum_{k=1..n} a_k sin(k x),
+// x = theta v with theta = dw dt_max <= pi, and 0 for v <= 0 or v >= 1 (truncation).
+// Block at shared address tb: theta, 3 pad floats, then a_1 .. a_{4 nq} (zeros past n).
+// Clenshaw's recurrence b_k = a_k + 2 cos(x) b_{k+1} - b_{k+2} gives the sum as b_1 sin(x):
+// two FP32 operations per term. sin(x) and 2 cos(x) come from Taylor polynomials in
+// y = x - pi/2 in [-pi/2, pi/2] (sin x = cos y, cos x = -sin y; truncation below 1e-9), so
+// that both stay accurate to a few FP32 ulps: the recurrence amplifies an error in cos(x) by
+// up to ~n^2 near x = 0.
+__device__ __forceinline__ float phi_trig(float v, uint32_t tb, int nq) {
+    const float theta = lds_f1(tb);
+    const float y = fmaf(theta, v, -1.57079632679489662f);
+    const float y2 = y * y;
+    // 2 cos x = -2 sin y = y (-2 + y^2 (2/3! - y^2 (2/5! - ...)))
+    float c2 = fmaf(y2, -3.2118088e-10f, 5.0104217e-8f);      // -2/13!, 2/11!
+    c2 = fmaf(c2, y2, -5.5114638e-6f);                         // -2/9!
+    c2 = fmaf(c2, y2, 3.9682540e-4f);                          // 2/7!
+    c2 = fmaf(c2, y2, -1.6666667e-2f);                         // -2/5!
+    c2 = fmaf(c2, y2, 3.3333333e-1f);                          // 2/3!
+    c2 = fmaf(c2, y2, -2.0f);
+    c2 *= y;
+    // sin x = cos y = 1 - y^2/2! + y^4/4! - ...
+    float sx = fmaf(y2, 2.0876757e-9f, -2.7557319e-7f);        // 1/12!, -1/10!
+    sx = fmaf(sx, y2, 2.4801587e-5f);                          // 1/8!
+    sx = fmaf(sx, y2, -1.3888889e-3f);                         // -1/6!
+    sx = fmaf(sx, y2, 4.1666667e-2f);                          // 1/4!
+    sx = fmaf(sx, y2, -0.5f);
+    sx = fmaf(sx, y2, 1.0f);
+    float b1 = 0.0f, b2 = 0.0f;
+    uint32_t pa = tb + 16u * (uint32_t)nq;   // group nq holds a_{4nq-3} .. a_{4nq}
+#pragma unroll 2
+    for (int q = nq; q > 0; --q, pa -= 16u) {
+        const float4 a = lds_f4(pa);
+        float b0 = fmaf(c2, b1, a.w - b2);
+        b2 = fmaf(c2, b0, a.z - b1);
+        b1 = fmaf(c2, b2, a.y - b0);
+        b0 = fmaf(c2, b1, a.x - b2);
+        // after the four steps: (b_k, b_{k+1}) = (b0, b1)
+        b2 = b1;
+        b1 = b0;
+    }
+    const float S = b1 * sx;
+    return (v > 0.0f && v < 1.0f) ? S : 0.0f;
+}
+
+// phi_trig for N values of one band at once: the N recurrences run interleaved (independent
+// chains for the scheduler) and share each shared-memory load of four coefficients.
+template <int N>
+__device__ __forceinline__ void phi_trig_n(const float* v, uint32_t tb, int nq, float* out) {
+    const float theta = lds_f1(tb);
+    float c2[N], sx[N], b1[N], b2[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const float y = fmaf(theta, v[i], -1.57079632679489662f);
+        const float y2 = y * y;
+        float c = fmaf(y2, -3.2118088e-10f, 5.0104217e-8f);
+        c = fmaf(c, y2, -5.5114638e-6f);
+        c = fmaf(c, y2, 3.9682540e-4f);
+        c = fmaf(c, y2, -1.6666667e-2f);
+        c = fmaf(c, y2, 3.3333333e-1f);
+        c = fmaf(c, y2, -2.0f);
+        c2[i] = c * y;
+        float t = fmaf(y2, 2.0876757e-9f, -2.7557319e-7f);
+        t = fmaf(t, y2, 2.4801587e-5f);
+        t = fmaf(t, y2, -1.3888889e-3f);
+        t = fmaf(t, y2, 4.1666667e-2f);
+        t = fmaf(t, y2, -0.5f);
+        sx[i] = fmaf(t, y2, 1.0f);
+        b1[i] = 0.0f;
+        b2[i] = 0.0f;
+    }
+    uint32_t pa = tb + 16u * (uint32_t)nq;
+    for (int q = nq; q > 0; --q, pa -= 16u) {
+        const float4 a = lds_f4(pa);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            float b0 = fmaf(c2[i], b1[i], a.w - b2[i]);
+            float bb = fmaf(c2[i], b0, a.z - b1[i]);
+            float ba = fmaf(c2[i], bb, a.y - b0);
+            b0 = fmaf(c2[i], ba, a.x - bb);
+            b2[i] = ba;
+            b1[i] = b0;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) out[i] = (v[i] > 0.0f && v[i] < 1.0f) ? b1[i] * sx[i] : 0.0f;
 }
 
 // The same from a band table in global memory (n_tab entries).

@@ -216,12 +216,24 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     FFT_CUDA(cudaGetDevice(&dev));
     for (int b = 0; b < n_tables; ++b) {
         FFT_ARG(tables[b], "fft_geom_create: null table");
-        FFT_ARG(tables[b]->n == tables[0]->n, "fft_geom_create: all tables must have the same sample count");
+        FFT_ARG(tables[b]->kind == tables[0]->kind,
+                "fft_geom_create: tables must be all sampled tables or all sine series");
+        if (tables[0]->kind == PHI_TABLE)
+            FFT_ARG(tables[b]->n == tables[0]->n, "fft_geom_create: all tables must have the same sample count");
         if (tables[b]->dev != dev) {
             set_error("fft_geom_create: table was built on another device");
             return FFT_ERR_STATE;
         }
     }
+    const int32_t phi_kind = tables[0]->kind;
+    FFT_ARG(phi_kind == PHI_TABLE || dt_mode == FFT_DT_STABLE,
+            "fft_geom_create: sine-series tables need dt_mode FFT_DT_STABLE");
+    // device layout of one band's Phi: n_tab float2 entries. Series: a 16-byte header (theta =
+    // dw dt_max, the series argument at the cut-off) and the coefficients in groups of 4.
+    int32_t trig_terms = 0;
+    for (int b = 0; b < n_tables; ++b) trig_terms = std::max(trig_terms, tables[b]->n);
+    const int32_t trig_nq = (trig_terms + 3) / 4;
+    const int32_t n_tab = phi_kind == PHI_TABLE ? tables[0]->n : 2 + 2 * trig_nq;
     const int64_t V = (int64_t)grid->nx * grid->ny * grid->nz;
     FFT_ARG(V < ((int64_t)1 << 40), "fft_geom_create: grid too large");
     for (int64_t p = 0; p < n_rows; ++p) {
@@ -234,7 +246,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     {
         int optin = 0;
         FFT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        size_t need = (((size_t)n_tables * tables[0]->n * sizeof(float2) + 15) & ~(size_t)15) +
+        size_t need = (((size_t)n_tables * n_tab * sizeof(float2) + 15) & ~(size_t)15) +
                       (size_t)APPLY_WARPS * 96 * sizeof(float4);
         if (need > (size_t)optin) {
             set_error("fft_geom_create: the tables (n_tables x n_samples x 8 bytes) do not fit in shared memory");
@@ -249,8 +261,11 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     g->grid = *grid;
     g->c0 = c0;
     g->n_bands = n_tables;
-    g->n_tab = tables[0]->n;
+    g->n_tab = n_tab;
     g->dt_mode = dt_mode;
+    g->phi_kind = phi_kind;
+    g->trig_nq = phi_kind == PHI_TRIG ? trig_nq : 0;
+    g->trig_terms = phi_kind == PHI_TRIG ? trig_terms : 0;
     g->guard = false;
     fft_status rc = FFT_OK;
 #define GEOM_TRY(x)              \
@@ -279,13 +294,24 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
         hb[b].U = U;
         hb[b].h = (float)(grid->h / U);
         for (int a = 0; a < 3; ++a) hb[b].org[a] = (float)(grid->origin[a] / U);
-        // Is the table's last interior sample (just below the cut-off) non-negligible?
-        std::vector<double> phi(tables[b]->n);
-        cudaError_t ce = cudaMemcpy(phi.data(), tables[b]->d_phi, sizeof(double) * phi.size(), cudaMemcpyDeviceToHost);
-        if (ce != cudaSuccess) {
-            rc = cuda_fail(ce, "fft_geom_create: table copy");
-            free_geom(g);
-            return rc;
+        // Is Phi just below the cut-off non-negligible? (table: its sample at dt_max)
+        std::vector<double> phi;
+        if (phi_kind == PHI_TABLE) {
+            phi.resize(tables[b]->n);
+            cudaError_t ce = cudaMemcpy(phi.data(), tables[b]->d_phi, sizeof(double) * phi.size(), cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) {
+                rc = cuda_fail(ce, "fft_geom_create: table copy");
+                free_geom(g);
+                return rc;
+            }
+        } else {   // the series on 4096 points of [0, dt_max]
+            phi.resize(4096);
+            for (size_t k = 0; k < phi.size(); ++k) {
+                const double dt = tables[b]->dt_max * (double)k / (double)(phi.size() - 1);
+                double acc = 0.0;
+                for (int j = 1; j <= tables[b]->n; ++j) acc += tables[b]->coef[j - 1] * sin(j * tables[b]->dw * dt);
+                phi[k] = acc;
+            }
         }
         double mx = 0.0;
         for (double v : phi) mx = fmax(mx, fabs(v));
@@ -302,10 +328,22 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
 
     // ---- tables in the device layout
     GEOM_TRY(dmalloc(g, &g->tab, (size_t)n_tables * g->n_tab));
-    for (int b = 0; b < n_tables; ++b) {
-        pack_table_kernel<<<(unsigned)ceil_div(g->n_tab, 256), 256>>>(tables[b]->d_phi, g->n_tab,
-                                                                        g->tab + (size_t)b * g->n_tab);
-        GEOM_CUDA(cudaGetLastError());
+    if (phi_kind == PHI_TABLE) {
+        for (int b = 0; b < n_tables; ++b) {
+            pack_table_kernel<<<(unsigned)ceil_div(g->n_tab, 256), 256>>>(tables[b]->d_phi, g->n_tab,
+                                                                            g->tab + (size_t)b * g->n_tab);
+            GEOM_CUDA(cudaGetLastError());
+        }
+    } else {
+        // per band: (theta, 0), (0, 0), then a_1 .. a_{4 nq} as float pairs (zeros past n)
+        std::vector<float2> packed((size_t)n_tables * n_tab, make_float2(0.0f, 0.0f));
+        for (int b = 0; b < n_tables; ++b) {
+            float2* blk = packed.data() + (size_t)b * n_tab;
+            blk[0].x = (float)(tables[b]->dw * tables[b]->dt_max);
+            float* a = reinterpret_cast<float*>(blk + 2);
+            for (int j = 0; j < tables[b]->n; ++j) a[j] = (float)tables[b]->coef[j];
+        }
+        GEOM_CUDA(cudaMemcpy(g->tab, packed.data(), sizeof(float2) * packed.size(), cudaMemcpyHostToDevice));
     }
 
     // ---- row records
@@ -525,5 +563,6 @@ extern "C" fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info) {
     info->evaluated_evals = g->evaluated;
     info->scratch_bytes = g->scratch_bytes;
     info->dt_mode = g->dt_mode;
+    info->phi_terms = g->trig_terms;
     return FFT_OK;
 }

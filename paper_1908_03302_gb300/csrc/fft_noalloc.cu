@@ -97,6 +97,7 @@ extern "C" fft_status fft_psf_noalloc(fft_geom g, int64_t spike_vox, const int32
     FFT_ARG(g && out_dev, "fft_psf_noalloc: null argument");
     FFT_ARG(n_rows >= 0 && (n_rows == 0 || rows_dev), "fft_psf_noalloc: need n_rows >= 0 and rows_dev");
     FFT_ARG(spike_vox >= 0 && spike_vox < g->V, "fft_psf_noalloc: spike voxel out of range");
+    FFT_ARG(g->phi_kind == PHI_TABLE, "fft_psf_noalloc: needs a geometry built from sampled tables (not sine series)");
     if (g->M > NOALLOC_MAX_ROWS) {
         set_error("fft_psf_noalloc: the geometry has more rows than the static scratch holds (4194304)");
         return FFT_ERR_ARG;

@@ -224,6 +224,7 @@ extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_
     FFT_ARG(n_spike >= 1 && n_subsets >= 1, "fft_psf_batch: need at least one spike and one subset");
     FFT_ARG(mode == 0 || mode == 1, "fft_psf_batch: mode must be 0 (FP32) or 1 (BF16 tensor cores)");
     FFT_ARG(mode == 0 || n_subsets <= 32, "fft_psf_batch: the tensor-core path takes at most 32 subsets");
+    FFT_ARG(g->phi_kind == PHI_TABLE, "fft_psf_batch: needs a geometry built from sampled tables (not sine series)");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
     for (int k = 0; k < n_spike; ++k)

@@ -170,3 +170,52 @@ extern "C" void fft_table_destroy(fft_table t) {
     if (cur != t->dev) cudaSetDevice(cur);
     delete t;
 }
+
+// Sine-series form of Phi (Sec. II-C: coefficients and arguments of the trigonometric terms
+// of Eq. Kernel_freq). Both integrals by the rectangle rule on the nodes w_j = j dw; for the
+// even Gaussian W the denominator is int_0^inf w^2 W dw = sqrt(2 pi) s (w0^2 + s^2).
+extern "C" fft_status fft_trig_build(const fft_spectrum* spec, double dt_max, int32_t n_terms, double* coef_out,
+                                     double* dw_out, int32_t* n_terms_out, fft_table* out) {
+    FFT_ARG(spec && out, "fft_trig_build: null spec or out");
+    FFT_ARG(dt_max > 0 && isfinite(dt_max), "fft_trig_build: dt_max must be > 0");
+    FFT_ARG(spec->kind == 0, "fft_trig_build: the sine series needs a Gaussian spectrum (kind 0)");
+    FFT_ARG(spec->f_center_hz > 0 && spec->f_sigma_hz > 0 && isfinite(spec->f_center_hz) &&
+                isfinite(spec->f_sigma_hz),
+            "fft_trig_build: Gaussian spectrum needs f_center_hz > 0 and f_sigma_hz > 0");
+    FFT_ARG(n_terms >= 0 && n_terms <= TRIG_MAX_TERMS, "fft_trig_build: n_terms must be in [0, 256]");
+    *out = nullptr;
+    const double w0 = 2.0 * M_PI * spec->f_center_hz, s = 2.0 * M_PI * spec->f_sigma_hz;
+    const double T = fmax(2.0 * dt_max, dt_max + 6.5 / s);   // series period
+    const double dw = 2.0 * M_PI / T;
+    int n = n_terms;
+    if (n == 0) {
+        const double nn = ceil((w0 + 5.5 * s) / dw);   // W < 3e-7 beyond
+        if (!(nn >= 1.0) || nn > TRIG_MAX_TERMS) {
+            set_error("fft_trig_build: the automatic term count exceeds 256 (spectrum too wide for dt_max)");
+            return FFT_ERR_ARG;
+        }
+        n = (int)nn;
+    }
+    int dev = 0;
+    FFT_CUDA(cudaGetDevice(&dev));
+    const double den = sqrt(2.0 * M_PI) * s * (w0 * w0 + s * s);
+    fft_table t = new fft_table_s();
+    t->dev = dev;
+    t->n = n;
+    t->dt_max = dt_max;
+    t->d_phi = nullptr;
+    t->kind = PHI_TRIG;
+    t->dw = dw;
+    t->coef.resize(n);
+    for (int j = 1; j <= n; ++j) {
+        const double w = j * dw, a = (w - w0) / s, b = (w + w0) / s;
+        const double W = exp(-0.5 * a * a) + exp(-0.5 * b * b);
+        t->coef[j - 1] = dw * w * w * w * W / den;
+    }
+    if (coef_out)
+        for (int j = 0; j < n; ++j) coef_out[j] = t->coef[j];
+    if (dw_out) *dw_out = dw;
+    if (n_terms_out) *n_terms_out = n;
+    *out = t;
+    return FFT_OK;
+}
