@@ -72,6 +72,7 @@ def lib():
             L.oracle_J_entry.restype = d
             L.oracle_J.argtypes = geom + [i64, vp, i64, vp, vp]
             L.oracle_JT.argtypes = geom + [i64, vp, vp, i64, vp]
+            L.oracle_coverage.argtypes = geom + [i64, vp, vp, i64, vp]
             L.oracle_count_support.argtypes = geom + [i64, vp, i64]
             L.oracle_count_support.restype = i64
             L.oracle_frob2.argtypes = geom + [i64]
@@ -231,6 +232,20 @@ class Geometry:
             idx = np.ascontiguousarray(voxels, dtype=np.int64)
             out = np.empty(len(idx))
             lib().oracle_JT(*self._args(), self.M, _p(d), _p(idx), len(idx), _p(out))
+        return out
+
+    def coverage(self, w: Optional[np.ndarray] = None, voxels: Optional[np.ndarray] = None) -> np.ndarray:
+        """sum_p |J[p, v] w_p| for every voxel (or the given ones); w None: all ones."""
+        wp = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+        if wp is not None:
+            assert wp.shape == (self.M,)
+        if voxels is None:
+            out = np.empty(self.V)
+            lib().oracle_coverage(*self._args(), self.M, _p(wp), None, 0, _p(out))
+        else:
+            idx = np.ascontiguousarray(voxels, dtype=np.int64)
+            out = np.empty(len(idx))
+            lib().oracle_coverage(*self._args(), self.M, _p(wp), _p(idx), len(idx), _p(out))
         return out
 
     def count_support(self, rows: Optional[np.ndarray] = None) -> int:

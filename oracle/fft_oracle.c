@@ -33,6 +33,8 @@
  *                  the damped normal equations (CGLS form), m0 = 0, fixed iterations.
  *   PSF            Sec. II-D, Eq. resolution_2: the Hessian H = J^T J applied to a
  *                  point-localised perturbation e_k, over a subset of rows.
+ *   coverage       Sec. III-A: the absolute values of the operator's entries summed over
+ *                  the rows, per voxel (the sensitivity coverage of an acquisition).
  */
 #include <math.h>
 #include <stdint.h>
@@ -383,6 +385,37 @@ void oracle_JT(GEOM_ARGS, int64_t M, const double* d, const int64_t* vox_idx, in
             if (jv != 0.0) kadd(&acc, jv * d[p]);
         }
         gout[i] = acc.s;
+    }
+    free(box);
+    free(ok);
+}
+
+/* Sensitivity coverage (Sec. III-A): cov[i] = sum_p |J[p, vox_idx[i]] w[p]| over all M rows
+ * (w NULL: all ones; vox_idx NULL: all voxels). */
+void oracle_coverage(GEOM_ARGS, int64_t M, const double* w, const int64_t* vox_idx, int64_t n_sel,
+                     double* cov) {
+    GEOM_INIT;
+    int64_t V = (int64_t)nx * ny * nz;
+    int64_t n_out = vox_idx ? n_sel : V;
+    int64_t* box = (int64_t*)malloc(sizeof(int64_t) * 6 * (size_t)(M > 0 ? M : 1));
+    char* ok = (char*)malloc((size_t)(M > 0 ? M : 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < M; ++p) ok[p] = (char)row_box(g, p, box + 6 * p, box + 6 * p + 3);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n_out; ++i) {
+        int64_t v = vox_idx ? vox_idx[i] : i;
+        int64_t vi = v % nx, vj = (v / nx) % ny, vk = v / ((int64_t)nx * ny);
+        double x[3];
+        vox_centre(g, v, x);
+        ksum acc = {0, 0};
+        for (int64_t p = 0; p < M; ++p) {
+            const int64_t* b = box + 6 * p;
+            if (!ok[p] || vi < b[0] || vi > b[3] || vj < b[1] || vj > b[4] || vk < b[2] || vk > b[5]) continue;
+            double wp = w ? w[p] : 1.0;
+            if (wp == 0.0) continue;
+            kadd(&acc, fabs(jentry(g, p, x) * wp));
+        }
+        cov[i] = acc.s;
     }
     free(box);
     free(ok);
