@@ -26,6 +26,7 @@ import subprocess
 import sys
 import threading
 import time
+from typing import Optional
 
 import numpy as np
 
@@ -305,6 +306,79 @@ def run_psf(args, ws, rank, local):
     return 0
 
 
+# --------------------------------------------------------------------------- elevation spacing
+
+def fwhm(profile: np.ndarray, h: float, centre: int) -> Optional[float]:
+    """Full width at half maximum (m) of a PSF profile around its peak at index `centre`, by
+    linear interpolation between samples; None if it does not fall to half on both sides."""
+    p = np.asarray(profile, dtype=np.float64)
+    half = 0.5 * p[centre]
+    if not half > 0:
+        return None
+    edges = []
+    for step in (-1, 1):
+        i = centre
+        while 0 <= i + step < len(p) and p[i + step] > half:
+            i += step
+        if not 0 <= i + step < len(p):
+            return None
+        a, b = p[i], p[i + step]
+        edges.append(i + step * (a - half) / (a - b))
+    return abs(edges[1] - edges[0]) * h
+
+
+def run_spacing(args, ws, rank, local):
+    """Resolution against elevation spacing (Sec. III-C): Hessian PSFs H e_k = J^T J e_k with all
+    rows of a 256-element ring stacked at 3 mm (11 elevations) or 8 mm (7 elevations), for spikes
+    at x = 0, 20, 40, 60 mm on the mid plane; reports per PSF the peak, the vertical and
+    horizontal half-maximum widths through the spike and the deepest negative lobe (the
+    trade-offs) relative to the peak, and the GPU time of each batch (FP32 path)."""
+    import torch
+    import paper_1908_03302_gb300 as fg
+    torch.cuda.set_device(local)
+    xs_mm = (0, 20, 40, 60)
+    res = {}
+    for spacing, npos in ((3e-3, 11), (8e-3, 7)):
+        w = wl.elevation_stack(spacing, npos)
+        g = w.grid
+        tables = [fg.Table(b.f_center_hz, b.f_sigma_hz, b.n_samples, b.dt_max) for b in w.bands]
+        geo = fg.Geometry(w.tx, w.row_pairs(), g, w.c0, tables)
+        ic, kc = (g.nx - 1) // 2, (g.nz - 1) // 2
+        spikes = [(kc * g.ny + ic) * g.nx + ic + int(round(x * 1e-3 / g.h)) for x in xs_mm]
+        rows = np.arange(geo.M, dtype=np.int32)
+        out = torch.empty(len(spikes) * geo.V, device="cuda", dtype=torch.float32)
+        geo.psf_batch(spikes, [rows], mode=0, out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        geo.psf_batch(spikes, [rows], mode=0, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        psf = out.view(len(spikes), g.nz, g.ny, g.nx).double().cpu().numpy()
+        entry = {"elevations": npos, "rows": geo.M, "ms": a.elapsed_time(b), "psfs": []}
+        for x, v in zip(xs_mm, spikes):
+            i = v % g.nx
+            vert = psf[xs_mm.index(x), :, ic, i]
+            horz = psf[xs_mm.index(x), kc, ic, :]
+            fz, fx = fwhm(vert, g.h, kc), fwhm(horz, g.h, i)
+            # trade-offs: the deepest negative lobe relative to the peak, along z and along x
+            entry["psfs"].append({"x_mm": x, "peak": float(vert[kc]),
+                                  "fwhm_z_mm": None if fz is None else 1e3 * fz,
+                                  "fwhm_x_mm": None if fx is None else 1e3 * fx,
+                                  "neg_lobe_z": float(max(0.0, -vert.min()) / vert[kc]),
+                                  "neg_lobe_x": float(max(0.0, -horz.min()) / horz[i])})
+        res[f"{spacing * 1e3:.0f}mm"] = entry
+    if rank == 0:
+        print(json.dumps({"metric": "PSF widths and trade-offs for 3 mm vs 8 mm elevation spacing",
+                          "value": res["3mm"]["ms"] + res["8mm"]["ms"], "unit": "ms",
+                          "higher_is_better": False, "n_gpus": ws, "dtype": "f32",
+                          "data": "synthetic (seeded ring stacks, unit spikes)",
+                          "config": {"workload": "elevation spacing", "grid": "141 x 141 x 33 @ 1 mm",
+                                     "ring": "256 elements, 100 mm", "band": "1 MHz, sigma 0.4 MHz"},
+                          "spacing": res}), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def main():
@@ -313,7 +387,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ring256", choices=["ring32", "ring256", "slices3d", "psf3d"])
+    ap.add_argument("--workload", default="ring256",
+                    choices=["ring32", "ring256", "slices3d", "psf3d", "spacing"])
     ap.add_argument("--psf-spikes", type=int, default=128)
     ap.add_argument("--psf-fp32-spikes", type=int, default=8)
     ap.add_argument("--psf-geometry", default="slices3d", choices=["slices3d", "ring256"])
@@ -335,6 +410,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "psf3d":
         return run_psf(args, ws, rank, local)
+    if args.workload == "spacing":
+        return run_spacing(args, ws, rank, local)
 
     import torch
     import paper_1908_03302_gb300 as fg

@@ -170,6 +170,16 @@ fft_status fft_J_apply(fft_geom g, const float* m_dev, float* d_dev, void* strea
 fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev, void* stream);
 
 /*
+ * fft_coverage - sensitivity coverage cov_v = sum_p |J[p, v] w_p|: the absolute values of the
+ * operator's entries summed over the rows for every voxel (Sec. III-A, the coverage map of
+ * the experiment; with w = 1 it is J^T of |J| applied to ones).
+ *   w_dev    device float32[M] row weights (e.g. a 0/1 mask of a row subset), or NULL for 1.
+ *   cov_dev  device float32[V] (written entirely). Same gather as fft_JT_apply: no atomics,
+ *            deterministic.
+ */
+fft_status fft_coverage(fft_geom g, const float* w_dev, float* cov_dev, void* stream);
+
+/*
  * fft_frob2 - |J|_F^2 = sum over rows and voxels of J[p, v]^2, computed on the device with
  * FP64 accumulation; synchronous; cached in the handle after the first call.
  */

@@ -191,6 +191,16 @@ class Geometry:
                                        _stream_handle(stream)))
         return out
 
+    def coverage(self, w=None, out=None, device=None, stream=None):
+        """Sensitivity coverage sum_p |J[p, v] w_p| per voxel (w: optional row weights)."""
+        torch = _torch()
+        if out is None:
+            dev = w.device if w is not None else (device or torch.device("cuda", torch.cuda.current_device()))
+            out = torch.empty(self.V, device=dev, dtype=torch.float32)
+        check(_lib.load().fft_coverage(self.handle, None if w is None else _dev_ptr(w, self.M, "w"),
+                                       _dev_ptr(out, self.V, "cov"), _stream_handle(stream)))
+        return out
+
     def frob2(self) -> float:
         v = ctypes.c_double()
         check(_lib.load().fft_frob2(self.handle, ctypes.byref(v)))

@@ -70,6 +70,7 @@ SIGNATURES = {
     "fft_geom_info": (ctypes.c_int, [_VP, ctypes.POINTER(fft_geom_info_t)]),
     "fft_J_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_JT_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fft_coverage": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_frob2": (ctypes.c_int, [_VP, ctypes.POINTER(_D)]),
     "fft_cg_solve": (ctypes.c_int, [_VP, _VP, _D, _I32, _VP, _VP, _VP]),
     "fft_psf_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP, _I32, _VP, _I32, _VP, _VP]),

@@ -26,7 +26,8 @@
 
 namespace fftgb {
 
-enum { MODE_JT = 0, MODE_J = 1, MODE_COUNT = 2, MODE_FROB = 3 };
+// MODE_COV: sensitivity coverage sum_p |J[p, v] w_p| (J^T of |J|, same gather as MODE_JT)
+enum { MODE_JT = 0, MODE_J = 1, MODE_COUNT = 2, MODE_FROB = 3, MODE_COV = 4 };
 
 struct ApplyParams {
     const RowRec* rec;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                 const float hb = bc.h;
                 float W = r.b.w;
                 if (MODE == MODE_JT) W *= __ldg(P.vin + p);
+                if (MODE == MODE_COV) W = fabsf(W) * (P.vin ? fabsf(__ldg(P.vin + p)) : 1.0f);
                 const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
                 // sub-brick centres relative to the pair midpoint (FP32; used by the bound only)
                 const float dx = fmaf((float)TX, hb, bc.org[0]) - r.a.x;
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                 const float cy1 = fmaf(8.0f * wy + 5.5f, hb, dy);
                 const float hxx = 3.5f * hb, hyy = 1.5f * hb;
                 // rows with zero weight add exactly nothing to J^T: skip them
-                const bool live = (MODE != MODE_JT) || (W != 0.0f);
+                const bool live = (MODE != MODE_JT && MODE != MODE_COV) || (W != 0.0f);
                 ok0 = live && sub_ok0 && box_may_touch(cx, cy0, cz, ex, ey, ez, hl, hxx, hyy, hyy);
                 ok1 = live && sub_ok1 && box_may_touch(cx, cy1, cz, ex, ey, ez, hl, hxx, hyy, hyy);
                 // sub-bricks whose voxels all satisfy |p| <= hl (between the transducer planes)
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
         }                                                                                          \
         const float val = phi_lookup(v, tb, nm1) * (is * ir);                                      \
         if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                                  \
+        if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val), W, acc[s][t]);                          \
         if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                      \
         if (MODE == MODE_FROB) {                                                                   \
             if ((vmask >> (4 * s + t)) & 1u) part = fmaf(val, val, part);                          \
@@ -299,6 +302,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
         _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                      \
             const float val = ph[t] * ww[t];                                                       \
             if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                              \
+            if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val), W, acc[s][t]);                      \
             if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                  \
             if (MODE == MODE_FROB) {                                                               \
                 if ((vmask >> (4 * s + t)) & 1u) part = fmaf(val, val, part);                      \
@@ -370,6 +374,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
                             const float val1 = phi_eval<PHI>(v, tb, nm1, nq) * w;
                             const float val2 = phi_eval<PHI>(v2, tb, nm1, nq) * w;
                             if (MODE == MODE_JT) acc[s][t] = fmaf(val2 - val1, W, acc[s][t]);
+                            if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val2) - fabsf(val1), W, acc[s][t]);
                             if (MODE == MODE_J) part = fmaf(val2 - val1, mv[s][t], part);
                             if (MODE == MODE_FROB) {
                                 if ((vmask >> (4 * s + t)) & 1u) part += val2 * val2 - val1 * val1;
@@ -387,7 +392,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
             __syncwarp();
         }
 
-        if (MODE == MODE_JT) {
+        if (MODE == MODE_JT || MODE == MODE_COV) {
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 if (item.slot < 0) {
@@ -525,6 +530,7 @@ fft_status set_apply_attributes(fft_geom g) {
     if ((rc = set_attr_mode<MODE_JT>(smem)) != FFT_OK) return rc;
     if ((rc = set_attr_mode<MODE_J>(smem)) != FFT_OK) return rc;
     if ((rc = set_attr_mode<MODE_COUNT>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_mode<MODE_COV>(smem)) != FFT_OK) return rc;
     return set_attr_mode<MODE_FROB>(smem);
 }
 
@@ -601,6 +607,20 @@ fft_status launch_JT(fft_geom g, const float* din, float* gout, cudaStream_t st)
     return FFT_OK;
 }
 
+// cov_v = sum_p |J[p, v] w_p| (w null: all ones), gathered like J^T.
+fft_status launch_cov(fft_geom g, const float* w, float* cov, cudaStream_t st) {
+    ApplyParams P = make_params(g);
+    P.vin = w;
+    P.vout = cov;
+    fft_status rc = launch_mode<MODE_COV>(g, P, st);
+    if (rc != FFT_OK) return rc;
+    int64_t blocks = ceil_div(g->V, 256);
+    jt_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->tile_slot0, g->tile_nslot, g->gpart, g->grid.nx,
+                                                       g->grid.ny, g->grid.nz, g->tiles[0], g->tiles[1], cov);
+    FFT_CUDA(cudaGetLastError());
+    return FFT_OK;
+}
+
 // In-support evaluations (dt < dt_max) of one apply and evaluations actually performed.
 fft_status count_support(fft_geom g, int64_t* support, int64_t* evaluated) {
     ApplyParams P = make_params(g);
@@ -656,6 +676,13 @@ extern "C" fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev,
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
     return launch_JT(g, d_dev, g_dev, (cudaStream_t)stream);
+}
+
+extern "C" fft_status fft_coverage(fft_geom g, const float* w_dev, float* cov_dev, void* stream) {
+    FFT_ARG(g && cov_dev, "fft_coverage: null argument");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    return launch_cov(g, w_dev, cov_dev, (cudaStream_t)stream);
 }
 
 extern "C" fft_status fft_frob2(fft_geom g, double* out) {

@@ -238,6 +238,18 @@ def slices3d() -> Workload:
                     C0_WATER, cg_iters=20, lambda_rel=1e-3, model_seed=6, noise_seed=7)
 
 
+def elevation_stack(spacing: float, n_positions: int, n_tx: int = 256) -> Workload:
+    """One 100 mm ring of n_tx elements translated to n_positions elevations spaced by `spacing`
+    (centred on z = 0), pairs within each elevation, one band (1 MHz, sigma 0.4 MHz), on a
+    141 x 141 x 33 grid at 1 mm (a cylinder-sized ROI of radius 70 mm and height 32 mm, with
+    voxel centres on the axes). Used for the 3 mm vs 8 mm elevation-spacing comparison."""
+    zpos = [spacing * (k - (n_positions - 1) / 2.0) for k in range(n_positions)]
+    tx, pairs = slice_rings(n_tx, 100e-3, zpos)
+    return Workload(f"stack{int(round(spacing * 1e4))}", tx, pairs, np.zeros(len(pairs), np.int32),
+                    [Band(1.0e6, 0.4e6)], Grid.centred(141, 141, 33, 1e-3), C0_WATER, cg_iters=20,
+                    lambda_rel=1e-3)
+
+
 def ring_subsets(n_tx: int = 256, n_slices: int = 16, strides=(4, 2, 1), n_bands: int = 3) -> List[np.ndarray]:
     """Row subsets of a (band, slice, s, r) pair list: every 4th / 2nd / every element of each ring.
 
