@@ -426,18 +426,26 @@ __global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(con
 }
 
 // d_p = sum over the row's entries (ascending tile order) and the 8 warps of the partials.
-__global__ void j_reduce_kernel(const int64_t* __restrict__ row_off, const int64_t* __restrict__ row_ent,
-                                const float* __restrict__ jpart, int64_t M, float* __restrict__ d) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) j_reduce_kernel(const int64_t* __restrict__ row_off,
+                                                       const int64_t* __restrict__ row_ent,
+                                                       const float* __restrict__ jpart, int64_t M,
+                                                       float* __restrict__ d) {
+    // one warp per row: lane l takes the row's entries l, l + 32, ... in order (the 8 region
+    // partials of an entry pairwise in FP32, entries accumulated in FP64), then a fixed
+    // butterfly over the lanes; the order never depends on scheduling
+    const int lane = threadIdx.x & 31;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (p >= M) return;
     double s = 0.0;
-    for (int64_t j = row_off[p]; j < row_off[p + 1]; ++j) {
+    const int64_t j1 = row_off[p + 1];
+    for (int64_t j = row_off[p] + lane; j < j1; j += 32) {
         const float4* q = reinterpret_cast<const float4*>(jpart + row_ent[j] * 8);
-        float4 a = q[0], b = q[1];
-        s += (double)a.x + (double)a.y + (double)a.z + (double)a.w + (double)b.x + (double)b.y +
-             (double)b.z + (double)b.w;
+        const float4 a = __ldg(q), b = __ldg(q + 1);
+        s += (double)(((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w)));
     }
-    d[p] = (float)s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) d[p] = (float)s;
 }
 
 // g for voxels of tiles with several items (sum of slots in item order) or with none (0).
@@ -587,7 +595,7 @@ fft_status launch_J(fft_geom g, const float* m, float* d, cudaStream_t st) {
     fft_status rc = launch_mode<MODE_J>(g, P, st);
     if (rc != FFT_OK) return rc;
     if (g->M > 0) {
-        int64_t blocks = ceil_div(g->M, 256);
+        int64_t blocks = ceil_div(g->M, 8);   // 8 rows (warps) per block
         j_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->row_off, g->row_ent, g->jpart, g->M, d);
         FFT_CUDA(cudaGetLastError());
     }
