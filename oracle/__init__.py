@@ -73,6 +73,10 @@ def lib():
             L.oracle_J.argtypes = geom + [i64, vp, i64, vp, vp]
             L.oracle_JT.argtypes = geom + [i64, vp, vp, i64, vp]
             L.oracle_coverage.argtypes = geom + [i64, vp, vp, i64, vp]
+            L.oracle_J2d.argtypes = geom + [i64, vp, i64, vp, vp]
+            L.oracle_JT2d.argtypes = geom + [i64, vp, vp, i64, vp]
+            L.oracle_k2_midpoint.argtypes = [vp, vp, d, d, d, d, ctypes.c_int, d, vp, ctypes.c_int, d]
+            L.oracle_k2_midpoint.restype = d
             L.oracle_count_support.argtypes = geom + [i64, vp, i64]
             L.oracle_count_support.restype = i64
             L.oracle_frob2.argtypes = geom + [i64]
@@ -143,6 +147,15 @@ def phi_trig(a: np.ndarray, dw: float, dt_max: float, dt: float) -> float:
     """The truncated sine series at one dt (FP64, term by term)."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     return lib().oracle_phi_trig(_p(a), len(a), float(dw), float(dt_max), float(dt))
+
+
+def k2_midpoint(xs, xr, x: float, y: float, z0: float, hz: float, nz: int, c0: float, table: np.ndarray,
+                dt_max: float) -> float:
+    """int K0(x, y, z) dz over [z0, z0 + nz hz] by the midpoint rule (s^2 / m^3)."""
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (xs, xr)]
+    t = np.ascontiguousarray(table, dtype=np.float64)
+    return lib().oracle_k2_midpoint(_p(a[0]), _p(a[1]), float(x), float(y), float(z0), float(hz), int(nz), c0,
+                                    _p(t), len(t), dt_max)
 
 
 def detour(xs, xr, x):
@@ -232,6 +245,23 @@ class Geometry:
             idx = np.ascontiguousarray(voxels, dtype=np.int64)
             out = np.empty(len(idx))
             lib().oracle_JT(*self._args(), self.M, _p(d), _p(idx), len(idx), _p(out))
+        return out
+
+    def J2d(self, m2: np.ndarray, rows: Optional[np.ndarray] = None) -> np.ndarray:
+        """d = J2 m2: the operator integrated over the grid's z layers (Eq. forward_2D)."""
+        m2 = np.ascontiguousarray(m2, dtype=np.float64)
+        assert m2.shape == (self.grid.nx * self.grid.ny,)
+        idx = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.empty(self.M if idx is None else len(idx))
+        lib().oracle_J2d(*self._args(), self.M, _p(idx), 0 if idx is None else len(idx), _p(m2), _p(out))
+        return out
+
+    def JT2d(self, d: np.ndarray, pixels: Optional[np.ndarray] = None) -> np.ndarray:
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        assert d.shape == (self.M,)
+        idx = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
+        out = np.empty(self.grid.nx * self.grid.ny if idx is None else len(idx))
+        lib().oracle_JT2d(*self._args(), self.M, _p(d), _p(idx), 0 if idx is None else len(idx), _p(out))
         return out
 
     def coverage(self, w: Optional[np.ndarray] = None, voxels: Optional[np.ndarray] = None) -> np.ndarray:

@@ -35,6 +35,8 @@
  *                  point-localised perturbation e_k, over a subset of rows.
  *   coverage       Sec. III-A: the absolute values of the operator's entries summed over
  *                  the rows, per voxel (the sensitivity coverage of an acquisition).
+ *   J2, J2^T       Sec. II-B, Eq. forward_2D: the kernel integrated over z (midpoint rule on
+ *                  the grid's layers) acting on a plane map dc(x, y).
  */
 #include <math.h>
 #include <stdint.h>
@@ -388,6 +390,73 @@ void oracle_JT(GEOM_ARGS, int64_t M, const double* d, const int64_t* vox_idx, in
     }
     free(box);
     free(ok);
+}
+
+/* 2-D approximation (Sec. II-B, Eq. forward_2D): the kernel integrated over z by the midpoint
+ * rule on the grid's nz layers, times a plane map m2[j * nx + i]:
+ *   J2[p, (i, j)] = sum_k K0(x_i, y_j, z_k) h^3  (= h^2 * the z integral with spacing h). */
+void oracle_J2d(GEOM_ARGS, int64_t M, const int64_t* row_idx, int64_t n_sel, const double* m2, double* d) {
+    GEOM_INIT;
+    int64_t n_out = row_idx ? n_sel : M;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n_out; ++i) {
+        int64_t p = row_idx ? row_idx[i] : i;
+        int64_t lo[3], hi[3];
+        ksum acc = {0, 0};
+        if (row_box(g, p, lo, hi)) {
+            for (int64_t k = lo[2]; k <= hi[2]; ++k)
+                for (int64_t j = lo[1]; j <= hi[1]; ++j)
+                    for (int64_t ii = lo[0]; ii <= hi[0]; ++ii) {
+                        double x[3];
+                        vox_centre(g, (k * g->ny + j) * g->nx + ii, x);
+                        double jv = jentry(g, p, x);
+                        if (jv != 0.0) kadd(&acc, jv * m2[j * g->nx + ii]);
+                    }
+        }
+        d[i] = acc.s;
+    }
+}
+
+/* g2[(i, j)] = sum_p J2[p, (i, j)] d[p] for the pixels in pix_idx (NULL: all nx * ny). */
+void oracle_JT2d(GEOM_ARGS, int64_t M, const double* d, const int64_t* pix_idx, int64_t n_sel, double* g2) {
+    GEOM_INIT;
+    int64_t n2 = (int64_t)nx * ny;
+    int64_t n_out = pix_idx ? n_sel : n2;
+    int64_t* box = (int64_t*)malloc(sizeof(int64_t) * 6 * (size_t)(M > 0 ? M : 1));
+    char* ok = (char*)malloc((size_t)(M > 0 ? M : 1));
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < M; ++p) ok[p] = (char)row_box(g, p, box + 6 * p, box + 6 * p + 3);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n_out; ++i) {
+        int64_t u = pix_idx ? pix_idx[i] : i;
+        int64_t vi = u % nx, vj = u / nx;
+        ksum acc = {0, 0};
+        for (int64_t p = 0; p < M; ++p) {
+            const int64_t* b = box + 6 * p;
+            if (!ok[p] || d[p] == 0.0 || vi < b[0] || vi > b[3] || vj < b[1] || vj > b[4]) continue;
+            for (int64_t k = b[2]; k <= b[5]; ++k) {
+                double x[3];
+                vox_centre(g, (k * ny + vj) * nx + vi, x);
+                double jv = jentry(g, p, x);
+                if (jv != 0.0) kadd(&acc, jv * d[p]);
+            }
+        }
+        g2[i] = acc.s;
+    }
+    free(box);
+    free(ok);
+}
+
+/* The z integral of K0 at plane point (x, y) by the midpoint rule: nz nodes z0 + (k + 1/2) hz
+ * (s^2 / m^3); used to pin the 2-D rule's convergence. */
+double oracle_k2_midpoint(const double* xs, const double* xr, double x, double y, double z0, double hz, int nz,
+                          double c0, const double* tab, int n, double dt_max) {
+    ksum acc = {0, 0};
+    for (int k = 0; k < nz; ++k) {
+        double pt[3] = {x, y, z0 + (k + 0.5) * hz};
+        kadd(&acc, oracle_k0(xs, xr, pt, c0, tab, n, dt_max) * hz);
+    }
+    return acc.s;
 }
 
 /* Sensitivity coverage (Sec. III-A): cov[i] = sum_p |J[p, vox_idx[i]] w[p]| over all M rows
