@@ -507,6 +507,24 @@ def main():
         torch.cuda.synchronize()
         jt_ms.append(a.elapsed_time(b))
         j_ms.append(c.elapsed_time(e))
+    # the 2-D approximation (Eq. forward_2D) on the same geometry: the plane map and the
+    # kernel integrated over the grid's layers
+    j2_ms, jt2_ms = [], []
+    m2 = torch.randn(geo.V2, device=dev, dtype=torch.float32)
+    g2 = torch.empty(geo.V2, device=dev, dtype=torch.float32)
+    for i in range(3):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        geo.J2d(m2, out=dbuf)
+        b.record(stream)
+        c.record(stream)
+        geo.JT2d(r, out=g2)
+        e.record(stream)
+        torch.cuda.synchronize()
+        j2_ms.append(a.elapsed_time(b))
+        jt2_ms.append(c.elapsed_time(e))
     clocks = sampler.stop()
 
     # ---- end to end through the public API with host buffers
@@ -566,6 +584,7 @@ def main():
         "ms_per_J": 1e3 * j_avg, "ms_per_JT": 1e3 * jt_avg,
         "J_evals_per_s": support / j_avg, "JT_evals_per_s": support / jt_avg,
         "J_dense_equiv_per_s": geo.M * geo.V / j_avg, "JT_dense_equiv_per_s": geo.M * geo.V / jt_avg,
+        "ms_per_J2d": statistics.mean(j2_ms), "ms_per_JT2d": statistics.mean(jt2_ms),
         "setup_ms": {"table": 1e3 * (t1 - t0), "geometry_and_cull": 1e3 * (t2 - t1)},
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
                      "frac": achieved / peak_evals, "traffic": APPLY_TRAFFIC_BYTES,

@@ -180,6 +180,23 @@ fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev, void* stre
 fft_status fft_coverage(fft_geom g, const float* w_dev, float* cov_dev, void* stream);
 
 /*
+ * 2-D approximation (Sec. II-B, Eq. forward_2D): transducers in one plane, a model dc(x, y)
+ * that varies slowly in z over the kernels' extent; the kernel is integrated over z in
+ * [z0, z1] and the model lives on the plane. The geometry's grid supplies both: its nz layers
+ * are the z-quadrature nodes (midpoint rule, spacing h, the same rule as the volume
+ * integral), so J2[p, (i, j)] = sum_k J[p, (i, j, k)]. Choose the layers to cover the
+ * kernels' main contribution (the truncated support of the longest pair reaches
+ * |z| = sqrt(((L + c0 dt_max)/2)^2 - (L/2)^2)).
+ *   fft_J2d_apply   m2_dev device float32[nx * ny] (plane map, x fastest) -> d_dev float32[M].
+ *   fft_JT2d_apply  d_dev float32[M] -> g2_dev float32[nx * ny] (each pixel's sum over the
+ *                   layers in a fixed order; deterministic).
+ * Both use a volume scratch (V floats) owned by the geometry, allocated on first use; calls
+ * on one geometry must not overlap (as for all its calls).
+ */
+fft_status fft_J2d_apply(fft_geom g, const float* m2_dev, float* d_dev, void* stream);
+fft_status fft_JT2d_apply(fft_geom g, const float* d_dev, float* g2_dev, void* stream);
+
+/*
  * fft_frob2 - |J|_F^2 = sum over rows and voxels of J[p, v]^2, computed on the device with
  * FP64 accumulation; synchronous; cached in the handle after the first call.
  */

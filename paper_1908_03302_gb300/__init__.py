@@ -165,6 +165,7 @@ class Geometry:
         info = self.info()
         self.M = int(info.n_rows)
         self.V = int(info.n_vox)
+        self._grid_nz = int(grid.nz)
 
     def info(self) -> fft_geom_info_t:
         out = fft_geom_info_t()
@@ -189,6 +190,29 @@ class Geometry:
             out = torch.empty(self.V, device=d.device, dtype=torch.float32)
         check(_lib.load().fft_JT_apply(self.handle, _dev_ptr(d, self.M, "d"), _dev_ptr(out, self.V, "g"),
                                        _stream_handle(stream)))
+        return out
+
+    @property
+    def V2(self) -> int:
+        """Pixels of the plane (nx * ny) for the 2-D approximation."""
+        return self.V // self._grid_nz
+
+    def J2d(self, m2, out=None, stream=None):
+        """d = J2 m2 (Eq. forward_2D): the operator integrated over the grid's z layers."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.M, device=m2.device, dtype=torch.float32)
+        check(_lib.load().fft_J2d_apply(self.handle, _dev_ptr(m2, self.V2, "m2"), _dev_ptr(out, self.M, "d"),
+                                        _stream_handle(stream)))
+        return out
+
+    def JT2d(self, d, out=None, stream=None):
+        """g2 = J2^T d: J^T summed over the grid's z layers per pixel."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.V2, device=d.device, dtype=torch.float32)
+        check(_lib.load().fft_JT2d_apply(self.handle, _dev_ptr(d, self.M, "d"), _dev_ptr(out, self.V2, "g2"),
+                                         _stream_handle(stream)))
         return out
 
     def coverage(self, w=None, out=None, device=None, stream=None):

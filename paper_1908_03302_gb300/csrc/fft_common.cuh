@@ -150,6 +150,7 @@ struct fft_geom_s {
     double* cg_scal = nullptr;           // [8] device scalars
     double* cg_dots = nullptr;           // [2 * DOT_BLOCKS] partial inner products
     int32_t* cg_status = nullptr;        // [1]
+    float* vol = nullptr;                // [V] volume scratch of the 2-D apply (allocated on first use)
     double* cg_hist = nullptr;           // [cg_hist_cap]
     int32_t cg_hist_cap = 0;
     void* cg_graph = nullptr;            // cudaGraphExec_t of the iteration loop
