@@ -11,6 +11,8 @@ Contents:
   the Phi table by quadrature, the detour time, K0, J, J^T, the squared Frobenius norm,
   damped CGLS and Hessian PSFs, all in double precision (see that file's header for the
   section / equation each function follows).
+* ``lowrank.py``: the low-rank posterior covariance and resolution diagonals (randomized
+  subspace iteration over the oracle's J and J^T, numpy QR and eigh), FP64.
 * ``closed_form.py``: independent closed forms used to pin the C code: the Gaussian
   spectrum's Phi in closed form, prolate-spheroidal quadrature of the uniform-perturbation
   invariant, and a brute-force Born cross-correlation traveltime for a point scatterer.

@@ -266,6 +266,12 @@ def ring_subsets(n_tx: int = 256, n_slices: int = 16, strides=(4, 2, 1), n_bands
     return out
 
 
+def gaussian_block(n: int, b: int, seed: int) -> np.ndarray:
+    """(n, b) float64 standard normal test block (a randomized eigensolver's starting matrix),
+    columns stored contiguously when transposed: block.T is (b, n) C-ordered."""
+    return np.random.default_rng(seed).standard_normal((b, n)).T
+
+
 def model_for(w: Workload) -> np.ndarray:
     """The velocity perturbation (m/s, float64) that goes with a workload."""
     if w.name.startswith("ring32"):
