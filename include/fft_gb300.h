@@ -197,6 +197,40 @@ fft_status fft_J2d_apply(fft_geom g, const float* m2_dev, float* d_dev, void* st
 fft_status fft_JT2d_apply(fft_geom g, const float* d_dev, float* g2_dev, void* stream);
 
 /*
+ * fft_hessian_lowrank - the k dominant eigenpairs of the prior-preconditioned misfit Hessian
+ * H = J^T J / sigma^2 (Sec. II-D, Eq. low_rank, with Gamma_pr = I and Gamma_n^{-1} =
+ * I / sigma^2), by randomized subspace iteration (Halko, Martinsson and Tropp, SIAM Review 53,
+ * 2011, Algorithms 4.4 and 5.3):
+ *   Y = H Omega; n_power times { Q = orth(Y); Y = H Q }; Q = orth(Y);
+ *   T = Q^T H Q = U diag(l) U^T; V_k = Q U_k for the k largest l.
+ *   omega_dev  device float32, ell columns of length V (column j at omega_dev + j * V): the
+ *              starting block, drawn by the caller (e.g. standard normal); read only.
+ *   ell, k     1 <= k <= ell <= 256 (ell - k is the oversampling).
+ *   n_power    0 .. 64 power iterations.
+ *   sigma      noise standard deviation in s (> 0; 1 gives the eigenpairs of J^T J).
+ *   vecs_dev   device float32, k columns of length V: orthonormal eigenvectors, largest first.
+ *   eigvals    host double[k]: the eigenvalues, descending.
+ * H is applied with the J and J^T kernels, one column at a time ((n_power + 2) ell pairs of
+ * applications); orth is shifted Cholesky QR followed by two Cholesky QR passes with FP64
+ * Gram matrices; the ell x ell eigenproblem is solved on the host (cyclic Jacobi, FP64).
+ * Synchronous. Allocates two V x ell float32 blocks and small buffers per call.
+ * FFT_ERR_BREAKDOWN if an orthonormalisation fails (a zero or non-finite column).
+ */
+fft_status fft_hessian_lowrank(fft_geom g, const float* omega_dev, int32_t ell, int32_t k, int32_t n_power,
+                               double sigma, float* vecs_dev, double* eigvals, void* stream);
+
+/*
+ * fft_lowrank_diag - diagonals of the low-rank posterior covariance and resolution matrix
+ * (Eqs. posterior_app and resolution_app with Gamma_pr = I) from k eigenpairs of H:
+ *   res_v = sum_i d_i V[v, i]^2,  post_v = (1 - res_v) / alpha,  d_i = l_i / (l_i + alpha).
+ *   vecs_dev  device float32, k columns of length V; eigvals host double[k]; alpha > 0 the
+ *             damping of Eq. leastSquare_misfit.
+ *   post_dev, res_dev  device float32[V] outputs; either may be NULL. Synchronous.
+ */
+fft_status fft_lowrank_diag(fft_geom g, const float* vecs_dev, const double* eigvals, int32_t k, double alpha,
+                            float* post_dev, float* res_dev, void* stream);
+
+/*
  * fft_frob2 - |J|_F^2 = sum over rows and voxels of J[p, v]^2, computed on the device with
  * FP64 accumulation; synchronous; cached in the handle after the first call.
  */

@@ -215,6 +215,30 @@ class Geometry:
                                          _stream_handle(stream)))
         return out
 
+    def hessian_lowrank(self, omega, k: int, n_power: int = 1, sigma: float = 1.0, stream=None):
+        """k dominant eigenpairs of H = J^T J / sigma^2 by randomized subspace iteration from the
+        starting block omega (ell x V float32 CUDA tensor, one column per row). Returns
+        (eigenvalues as a numpy array, descending; eigenvectors as a k x V tensor)."""
+        torch = _torch()
+        if omega.dim() != 2 or omega.shape[1] != self.V:
+            raise ValueError("omega must be an (ell, V) tensor")
+        ell = int(omega.shape[0])
+        vecs = torch.empty((k, self.V), device=omega.device, dtype=torch.float32)
+        lam = np.empty(k)
+        check(_lib.load().fft_hessian_lowrank(self.handle, _dev_ptr(omega), ell, int(k), int(n_power), float(sigma),
+                                              _dev_ptr(vecs), lam.ctypes.data, _stream_handle(stream)))
+        return lam, vecs
+
+    def lowrank_diag(self, vecs, eigvals, alpha: float, stream=None):
+        """(diag of the low-rank posterior covariance, diag of the resolution matrix)."""
+        torch = _torch()
+        lam = np.ascontiguousarray(eigvals, dtype=np.float64)
+        post = torch.empty(self.V, device=vecs.device, dtype=torch.float32)
+        res = torch.empty(self.V, device=vecs.device, dtype=torch.float32)
+        check(_lib.load().fft_lowrank_diag(self.handle, _dev_ptr(vecs), lam.ctypes.data, len(lam), float(alpha),
+                                           _dev_ptr(post), _dev_ptr(res), _stream_handle(stream)))
+        return post, res
+
     def coverage(self, w=None, out=None, device=None, stream=None):
         """Sensitivity coverage sum_p |J[p, v] w_p| per voxel (w: optional row weights)."""
         torch = _torch()

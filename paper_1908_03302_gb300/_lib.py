@@ -73,6 +73,8 @@ SIGNATURES = {
     "fft_coverage": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_J2d_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_JT2d_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fft_hessian_lowrank": (ctypes.c_int, [_VP, _VP, _I32, _I32, _I32, _D, _VP, _VP, _VP]),
+    "fft_lowrank_diag": (ctypes.c_int, [_VP, _VP, _VP, _I32, _D, _VP, _VP, _VP]),
     "fft_frob2": (ctypes.c_int, [_VP, ctypes.POINTER(_D)]),
     "fft_cg_solve": (ctypes.c_int, [_VP, _VP, _D, _I32, _VP, _VP, _VP]),
     "fft_psf_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP, _I32, _VP, _I32, _VP, _VP]),
