@@ -211,10 +211,11 @@ fft_status fft_JT2d_apply(fft_geom g, const float* d_dev, float* g2_dev, void* s
  *   vecs_dev   device float32, k columns of length V: orthonormal eigenvectors, largest first.
  *   eigvals    host double[k]: the eigenvalues, descending.
  * H is applied with the J and J^T kernels, one column at a time ((n_power + 2) ell pairs of
- * applications); orth is shifted Cholesky QR followed by two Cholesky QR passes with FP64
- * Gram matrices; the ell x ell eigenproblem is solved on the host (cyclic Jacobi, FP64).
- * Synchronous. Allocates two V x ell float32 blocks and small buffers per call.
- * FFT_ERR_BREAKDOWN if an orthonormalisation fails (a zero or non-finite column).
+ * applications); orth is three SVQB passes (Gram matrix in FP64, its eigendecomposition on
+ * the host; directions below 1e-12 of the largest Gram eigenvalue are dropped, so a block
+ * wider than the rank of H is fine and yields zero Ritz values); the ell x ell eigenproblem is
+ * solved on the host (cyclic Jacobi, FP64). Synchronous. Allocates two V x ell float32 blocks
+ * and small buffers per call. FFT_ERR_BREAKDOWN if a block is zero or not finite.
  */
 fft_status fft_hessian_lowrank(fft_geom g, const float* omega_dev, int32_t ell, int32_t k, int32_t n_power,
                                double sigma, float* vecs_dev, double* eigvals, void* stream);

@@ -6,12 +6,12 @@
 // Review 53, 2011, Algorithms 4.4 and 5.3):
 //   Y = H Omega;  n_power times { Q = orth(Y); Y = H Q };  Q = orth(Y);
 //   T = Q^T (H Q) = U diag(l) U^T;  V_k = Q U_k (largest k).
-// H is applied column by column with the J and J^T kernels. orth is Cholesky QR with
-// Gram matrices accumulated in FP64: one pass on the Gram matrix shifted by a small multiple
-// of its trace (so that the factorisation exists even when Y is numerically rank-deficient),
-// then two plain passes (the shifted Cholesky QR3 of Fukaya, Kannan, Nakatsukasa, Yamamoto and
-// Yanagisawa, SIAM J. Sci. Comput. 42, 2020). The small dense steps (Cholesky, triangular
-// inverse, cyclic Jacobi eigensolver) run on the host in FP64 on ell x ell matrices.
+// H is applied column by column with the J and J^T kernels. orth is SVQB (Stathopoulos and
+// Wu, SIAM J. Sci. Comput. 23, 2002) applied three times: with the Gram matrix G = Y^T Y
+// (accumulated in FP64) and its eigendecomposition G = U D U^T, Q = Y U D^{-1/2}, where
+// directions with D below 1e-12 max D (numerically in the null space: a block wider than the
+// rank of H) are dropped as zero columns, which then give zero Ritz values. The small dense
+// steps (the cyclic Jacobi eigensolver) run on the host in FP64 on ell x ell matrices.
 //
 // Blocks are column-major: column j of a V x n block starts at j * V.
 #include <cuda_runtime.h>
@@ -126,38 +126,6 @@ __global__ void lowrank_diag_kernel(const float* __restrict__ vecs, const double
 
 // ---- host FP64 dense helpers (n <= MAX_ELL)
 
-// Upper-triangular R with R^T R = G (row-major n x n); false if a pivot is not positive.
-bool cholesky_upper(const std::vector<double>& G, int n, std::vector<double>& R) {
-    R.assign((size_t)n * n, 0.0);
-    for (int j = 0; j < n; ++j) {
-        double s = G[(size_t)j * n + j];
-        for (int k = 0; k < j; ++k) s -= R[(size_t)k * n + j] * R[(size_t)k * n + j];
-        if (!(s > 0.0)) return false;
-        const double rjj = sqrt(s);
-        R[(size_t)j * n + j] = rjj;
-        for (int i = j + 1; i < n; ++i) {
-            double t = G[(size_t)j * n + i];
-            for (int k = 0; k < j; ++k) t -= R[(size_t)k * n + j] * R[(size_t)k * n + i];
-            R[(size_t)j * n + i] = t / rjj;
-        }
-    }
-    return true;
-}
-
-// Inverse of an upper-triangular matrix (row-major), by back substitution column by column.
-std::vector<double> upper_inverse(const std::vector<double>& R, int n) {
-    std::vector<double> X((size_t)n * n, 0.0);
-    for (int c = 0; c < n; ++c) {
-        X[(size_t)c * n + c] = 1.0 / R[(size_t)c * n + c];
-        for (int i = c - 1; i >= 0; --i) {
-            double s = 0.0;
-            for (int k = i + 1; k <= c; ++k) s += R[(size_t)i * n + k] * X[(size_t)k * n + c];
-            X[(size_t)i * n + c] = -s / R[(size_t)i * n + i];
-        }
-    }
-    return X;
-}
-
 // Cyclic Jacobi eigensolver for a symmetric matrix (row-major, destroyed): eigenvalues in w,
 // eigenvectors in the columns of U (row-major n x n).
 void jacobi_eigen(std::vector<double>& A, int n, std::vector<double>& w, std::vector<double>& U) {
@@ -237,26 +205,26 @@ fft_status product(LowrankWork& W, const float* X, int n_in, const std::vector<d
     return FFT_OK;
 }
 
-// Q = orth(Y): shifted Cholesky QR, then two Cholesky QR passes (Y is overwritten).
+// Q = orth(Y): three SVQB passes, Y -> Q -> Y -> Q (Y is overwritten).
 fft_status orthonormalise(LowrankWork& W, float* Y, int n, float* Q) {
-    std::vector<double> G, R;
+    std::vector<double> G, d, U, Wm((size_t)n * n);
     for (int pass = 0; pass < 3; ++pass) {
-        float* src = pass == 0 ? Y : Q;
-        float* dst = pass == 1 ? Y : Q;   // ping-pong: Y -> Q -> Y -> Q
-        if (pass == 2) src = Y;
+        float* src = pass == 1 ? Q : Y;
+        float* dst = pass == 1 ? Y : Q;
         fft_status rc = gram(W, src, n, src, n, G, pass == 0);
         if (rc != FFT_OK) return rc;
-        if (pass == 0) {
-            double tr = 0.0;
-            for (int i = 0; i < n; ++i) tr += G[(size_t)i * n + i];
-            const double shift = 1e-7 * (tr > 0.0 ? tr : 1.0);
-            for (int i = 0; i < n; ++i) G[(size_t)i * n + i] += shift;
-        }
-        if (!cholesky_upper(G, n, R)) {
-            set_error("fft_hessian_lowrank: Cholesky QR failed (the block has a zero or non-finite column)");
+        jacobi_eigen(G, n, d, U);
+        double dmax = 0.0;
+        for (int i = 0; i < n; ++i) dmax = fmax(dmax, d[i]);
+        if (!(dmax > 0.0) || !isfinite(dmax)) {
+            set_error("fft_hessian_lowrank: the block to orthonormalise is zero or not finite");
             return FFT_ERR_BREAKDOWN;
         }
-        if ((rc = product(W, src, n, upper_inverse(R, n), n, dst)) != FFT_OK) return rc;
+        for (int c = 0; c < n; ++c) {
+            const double sc = d[c] > 1e-12 * dmax ? 1.0 / sqrt(d[c]) : 0.0;
+            for (int i = 0; i < n; ++i) Wm[(size_t)i * n + c] = U[(size_t)i * n + c] * sc;
+        }
+        if ((rc = product(W, src, n, Wm, n, dst)) != FFT_OK) return rc;
     }
     return FFT_OK;
 }
