@@ -100,8 +100,17 @@ __device__ __forceinline__ float detour_v64(const RowRec64& r, double ox, double
     return (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
 }
 
+// Resident CTAs per SM the register budget is sized for: the stable-detour table kernels fit
+// 64 registers without spilling (4 CTAs, 32 warps per SM); the others keep 80 (3 CTAs) and
+// the sharp-band ones 128 (2 CTAs).
+template <int DT, bool SHARP, int PHI>
+constexpr int apply_min_blocks() {
+    return SHARP ? 2 : ((DT == FFT_DT_STABLE && PHI == PHI_TABLE) ? 4 : 3);
+}
+
 template <int MODE, int DT, bool GUARD, bool SHARP, int PHI>
-__global__ void __launch_bounds__(APPLY_THREADS, SHARP ? 2 : 3) apply_kernel(const __grid_constant__ ApplyParams P) {
+__global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI>())
+    apply_kernel(const __grid_constant__ ApplyParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* s_tab = reinterpret_cast<float2*>(smem);
     const int tab_len = P.n_bands * P.n_tab;
