@@ -248,10 +248,18 @@ double oracle_detour_naive(const double* xs, const double* xr, const double* x) 
     return a + b - L;
 }
 
-/* K0(x; xs, xr) of Eq. Kernel_freq (units s^2 / m^4). Zero at the transducers. */
+/* Is x exactly on one of the transducers? Tested on the coordinates themselves: the distances
+ * rebuilt in the pair frame round to ~1e-18 m instead of 0 there. */
+static int on_transducer(const double* xs, const double* xr, const double* x) {
+    return (x[0] == xs[0] && x[1] == xs[1] && x[2] == xs[2]) || (x[0] == xr[0] && x[1] == xr[1] && x[2] == xr[2]);
+}
+
+/* K0(x; xs, xr) of Eq. Kernel_freq (units s^2 / m^4). Zero at the transducers (its limit there
+ * depends on the direction of approach; Phi(0) = 0 makes the limit along the ray zero). */
 double oracle_k0(const double* xs, const double* xr, const double* x, double c0,
                  const double* tab, int n, double dt_max) {
     double R, rs, rr, L;
+    if (on_transducer(xs, xr, x)) return 0.0;
     oracle_detour(xs, xr, x, &R, &rs, &rr, &L);
     if (rs == 0.0 || rr == 0.0) return 0.0;
     double phi = oracle_phi(tab, n, dt_max, R / c0);
@@ -314,6 +322,7 @@ static inline double jentry(const orc_geom* g, int64_t p, const double* x) {
     const double* tab = g->tables + (int64_t)b * g->n_tab;
     if (g->trig_dw) {   /* K0 with the sine-series Phi */
         double R, rs, rr, L;
+        if (on_transducer(xs, xr, x)) return 0.0;
         oracle_detour(xs, xr, x, &R, &rs, &rr, &L);
         if (rs == 0.0 || rr == 0.0) return 0.0;
         double phi = oracle_phi_trig(tab, g->n_tab, g->trig_dw[b], g->dt_max[b], R / g->c0);

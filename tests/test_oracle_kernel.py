@@ -182,3 +182,18 @@ def test_support_count_matches_ellipsoid_volume():
     b2 = a * a - 0.02 ** 2
     vol = 4.0 / 3.0 * math.pi * a * b2 / h ** 3
     assert geo.count_support() == pytest.approx(vol, rel=5e-3)
+
+
+def test_k0_zero_exactly_at_the_transducers():
+    # K0 has no single limit at a transducer; the definition sets it to 0 there. For oblique
+    # pairs the pair-frame distance rounds to ~1e-18 m instead of 0, so the rule must look at
+    # the coordinates themselves.
+    tab, dtm = _tab()
+    rng = np.random.default_rng(12)
+    for _ in range(50):
+        xs, xr = rng.uniform(-0.05, 0.05, 3), rng.uniform(-0.05, 0.05, 3)
+        assert oracle.k0(xs, xr, xs, C0, tab, dtm) == 0.0
+        assert oracle.k0(xs, xr, xr.copy(), C0, tab, dtm) == 0.0
+        # a point 1 um away has a finite, non-zero value of at most the scale near the emitter
+        x = xs + 1e-6 * (xr - xs) / np.linalg.norm(xr - xs)
+        assert np.isfinite(oracle.k0(xs, xr, x, C0, tab, dtm))
