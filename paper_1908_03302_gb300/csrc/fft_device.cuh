@@ -74,15 +74,29 @@ __device__ __forceinline__ bool box_may_touch(float dx, float dy, float dz, floa
 // The caller passes ps = p + hl and pr = p - hl (the axial offsets from the emitter and the
 // receiver) directly, so that they can be stepped along a run of voxels.
 // RAW: return R / U unsaturated (the caller clamps), so that values just above 1 stay visible.
+// GUARD: K0 has no single value at a transducer (its limit depends on the direction of
+// approach); like the oracle, the guarded form gives 0 there. A voxel centre on a transducer
+// lands ~1e-7 band units off it after FP32 rounding, where the plain form would evaluate a huge
+// 1 / R_xs times a non-zero Phi; points within GUARD_R of a transducer are therefore taken as
+// on it (is = ir = 0, so the entry is 0).
+constexpr float GUARD_R2 = 1e-8f;   // (1e-4 band units)^2
+
 template <int DT, bool GUARD, bool INNER = false, bool RAW = false>
 __device__ __forceinline__ float detour_v(float ps, float pr, float q2, float hl, float& is, float& ir) {
     float ss = fmaf(ps, ps, q2), rr = fmaf(pr, pr, q2);
+    bool at_tx = false;
     if (GUARD) {
+        at_tx = (ss < GUARD_R2) || (rr < GUARD_R2);
         ss = fmaxf(ss, 1e-30f);
         rr = fmaxf(rr, 1e-30f);
     }
     is = rsqrt_approx(ss);
     ir = rsqrt_approx(rr);
+    if (GUARD && at_tx) {
+        is = 0.0f;
+        ir = 0.0f;
+        return 0.0f;
+    }
     if (DT == FFT_DT_NAIVE) {
         const float v = fmaf(ss, is, fmaf(rr, ir, -2.0f * hl));
         return RAW ? v : __saturatef(v);
