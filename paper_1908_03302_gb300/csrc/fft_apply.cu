@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "fft_common.cuh"
@@ -236,23 +237,29 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                 uint32_t fix = 0;
                 // lane base (sub-brick 0, t = 0) in the pair frame: small offsets added to the
                 // tile origin's FP64-derived values
-                const float off = fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
-                float psb = A.x + off, prb = A.y + off;
-                float c1 = fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
-                float c2 = fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
-                float c3 = fmaf(Xl, hy, fmaf(-Yl, hx, B.w));
                 float part = 0.0f;
+                // The entry's evaluation, specialised for planar pairs (both transducers at one
+                // z: the axis has no z component, so h_z = 0 exactly and c1, c2 do not change
+                // along the lane's voxels or between the two sub-bricks).
+                auto entry_body = [&](auto planar_tag) {
+                    constexpr bool PL = decltype(planar_tag)::value;
+                const float off = PL ? fmaf(Xl, hx, Yl * hy) : fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
+                float psb = A.x + off, prb = A.y + off;
+                float c1 = PL ? fmaf(-Zl, hy, A.z) : fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
+                const float c2 = PL ? fmaf(Zl, hx, A.w) : fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
+                float c3 = fmaf(Xl, hy, fmaf(-Yl, hx, B.w));
+                const float c12_planar = PL ? fmaf(c2, c2, c1 * c1) : 0.0f;
 #pragma unroll
                 for (int s = 0; s < 2; ++s) {
                     const uint32_t ms = s ? m1 : m0;
                     if (s == 1) {
                         psb = fmaf(4.0f, hy, psb);
                         prb = fmaf(4.0f, hy, prb);
-                        c1 = fmaf(4.0f, hz, c1);
+                        if (!PL) c1 = fmaf(4.0f, hz, c1);
                         c3 = fmaf(-4.0f, hx, c3);
                     }
                     if (!((ms >> bit) & 1u)) continue;
-                    const float c1sq = c1 * c1;
+                    const float c1sq = PL ? 0.0f : c1 * c1;
                     const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
 #define FFT_EVAL_SUB(INNER_V, PLANAR_V)                                                              \
     float vv[NX_LANE], ww[NX_LANE];                                                                \
@@ -318,22 +325,19 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
             }                                                                                      \
         }                                                                                          \
     }
-                    const float c12sq = fmaf(c2, c2, c1sq);
+                    const float c12sq = PL ? c12_planar : fmaf(c2, c2, c1sq);
                     if (inner) {
-                        if (planar) {
-                            FFT_EVAL_SUB(true, true)
-                        } else {
-                            FFT_EVAL_SUB(true, false)
-                        }
+                        FFT_EVAL_SUB(true, PL)
                     } else {
-                        if (planar) {
-                            FFT_EVAL_SUB(false, true)
-                        } else {
-                            FFT_EVAL_SUB(false, false)
-                        }
+                        FFT_EVAL_SUB(false, PL)
                     }
-#undef FFT_EVAL_SUB
                 }
+                };
+                if (planar)
+                    entry_body(std::true_type{});
+                else
+                    entry_body(std::false_type{});
+#undef FFT_EVAL_SUB
                 if (SHARP && DT != FFT_DT_FP64 && __any_sync(0xffffffffu, fix != 0u)) {
                     // Re-decide dt < dt_max in FP64 for the flagged voxels and correct what the
                     // FP32 pass added (the FP32 value is recomputed by the same operations).

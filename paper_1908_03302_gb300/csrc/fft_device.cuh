@@ -54,10 +54,12 @@ __device__ __forceinline__ bool box_may_touch(float dx, float dy, float dz, floa
                                               float ez, float hl, float hx, float hy, float hz) {
     float sx = dx + hl * ex, sy = dy + hl * ey, sz = dz + hl * ez;   // c - xs
     float rx = dx - hl * ex, ry = dy - hl * ey, rz = dz - hl * ez;   // c - xr
-    float Rs = sqrtf(sx * sx + sy * sy + sz * sz);
-    float Rr = sqrtf(rx * rx + ry * ry + rz * rz);
-    if (!(Rs > 1e-6f) || !(Rr > 1e-6f)) return true;
-    float is = 1.0f / Rs, ir = 1.0f / Rr;
+    const float ss = sx * sx + sy * sy + sz * sz, rr = rx * rx + ry * ry + rz * rz;
+    if (!(ss > 1e-12f) || !(rr > 1e-12f)) return true;
+    // approximate reciprocal square roots (relative error ~1e-7): the bound's error is a few
+    // 1e-5 band units at most, far inside CULL_MARGIN
+    const float is = rsqrt_approx(ss), ir = rsqrt_approx(rr);
+    const float Rs = ss * is, Rr = rr * ir;
     float gx = sx * is + rx * ir, gy = sy * is + ry * ir, gz = sz * is + rz * ir;
     float lb = (Rs + Rr - 2.0f * hl) - (fabsf(gx) * hx + fabsf(gy) * hy + fabsf(gz) * hz);
     return !(lb >= 1.0f + CULL_MARGIN);   // NaN keeps the entry
