@@ -170,6 +170,22 @@ fft_status fft_J_apply(fft_geom g, const float* m_dev, float* d_dev, void* strea
 fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev, void* stream);
 
 /*
+ * fft_J_apply_batch / fft_JT_apply_batch - J or J^T applied to n vectors at once (the
+ * operator of Eq. forward_compact and its adjoint, for block methods such as the low-rank
+ * eigensolver): every evaluated entry J[p, v] is used for four columns, so a group of four
+ * costs little more than one application.
+ *   m_dev  device float32, n columns of length V (column c at m_dev + c * V);
+ *   d_dev  device float32, n columns of length M (column c at d_dev + c * M);
+ *   g_dev  device float32, n columns of length V.
+ * Columns are processed in groups of four; a remainder (and every column of geometries with
+ * a non-stable detour mode) goes through the single-vector kernels. Each column matches the
+ * single-vector call to rounding (same entries, same summation order). The first call
+ * allocates the handle's four-column scratch (E * 32 + slots * 4 * 2048 floats).
+ */
+fft_status fft_J_apply_batch(fft_geom g, const float* m_dev, int32_t n, float* d_dev, void* stream);
+fft_status fft_JT_apply_batch(fft_geom g, const float* d_dev, int32_t n, float* g_dev, void* stream);
+
+/*
  * fft_coverage - sensitivity coverage cov_v = sum_p |J[p, v] w_p|: the absolute values of the
  * operator's entries summed over the rows for every voxel (Sec. III-A, the coverage map of
  * the experiment; with w = 1 it is J^T of |J| applied to ones).
@@ -210,8 +226,8 @@ fft_status fft_JT2d_apply(fft_geom g, const float* d_dev, float* g2_dev, void* s
  *   sigma      noise standard deviation in s (> 0; 1 gives the eigenpairs of J^T J).
  *   vecs_dev   device float32, k columns of length V: orthonormal eigenvectors, largest first.
  *   eigvals    host double[k]: the eigenvalues, descending.
- * H is applied with the J and J^T kernels, one column at a time ((n_power + 2) ell pairs of
- * applications); orth is three SVQB passes (Gram matrix in FP64, its eigendecomposition on
+ * H is applied with the batch J and J^T kernels, four columns at a time ((n_power + 2) ell
+ * columns in all); orth is three SVQB passes (Gram matrix in FP64, its eigendecomposition on
  * the host; directions below 1e-12 of the largest Gram eigenvalue are dropped, so a block
  * wider than the rank of H is fine and yields zero Ritz values); the ell x ell eigenproblem is
  * solved on the host (cyclic Jacobi, FP64). Synchronous. Allocates two V x ell float32 blocks

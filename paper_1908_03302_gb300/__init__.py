@@ -192,6 +192,30 @@ class Geometry:
                                        _stream_handle(stream)))
         return out
 
+    def J_batch(self, m, out=None, stream=None):
+        """d[c] = J m[c] for the rows of m ((n, V) float32 CUDA tensor) -> (n, M)."""
+        torch = _torch()
+        if m.dim() != 2 or m.shape[1] != self.V:
+            raise ValueError("m must be an (n, V) tensor")
+        n = int(m.shape[0])
+        if out is None:
+            out = torch.empty((n, self.M), device=m.device, dtype=torch.float32)
+        check(_lib.load().fft_J_apply_batch(self.handle, _dev_ptr(m), n, _dev_ptr(out, n * self.M, "d"),
+                                            _stream_handle(stream)))
+        return out
+
+    def JT_batch(self, d, out=None, stream=None):
+        """g[c] = J^T d[c] for the rows of d ((n, M) float32 CUDA tensor) -> (n, V)."""
+        torch = _torch()
+        if d.dim() != 2 or d.shape[1] != self.M:
+            raise ValueError("d must be an (n, M) tensor")
+        n = int(d.shape[0])
+        if out is None:
+            out = torch.empty((n, self.V), device=d.device, dtype=torch.float32)
+        check(_lib.load().fft_JT_apply_batch(self.handle, _dev_ptr(d), n, _dev_ptr(out, n * self.V, "g"),
+                                             _stream_handle(stream)))
+        return out
+
     @property
     def V2(self) -> int:
         """Pixels of the plane (nx * ny) for the 2-D approximation."""

@@ -71,6 +71,8 @@ SIGNATURES = {
     "fft_J_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_JT_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_coverage": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "fft_J_apply_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP]),
+    "fft_JT_apply_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP]),
     "fft_J2d_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_JT2d_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_hessian_lowrank": (ctypes.c_int, [_VP, _VP, _I32, _I32, _I32, _D, _VP, _VP, _VP]),

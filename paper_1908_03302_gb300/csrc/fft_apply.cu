@@ -27,8 +27,11 @@
 
 namespace fftgb {
 
-// MODE_COV: sensitivity coverage sum_p |J[p, v] w_p| (J^T of |J|, same gather as MODE_JT)
-enum { MODE_JT = 0, MODE_J = 1, MODE_COUNT = 2, MODE_FROB = 3, MODE_COV = 4 };
+// MODE_COV: sensitivity coverage sum_p |J[p, v] w_p| (J^T of |J|, same gather as MODE_JT).
+// MODE_JT4 / MODE_J4: J^T and J for four right-hand sides at once (every evaluated entry is
+// applied to all four; blocks are column-major: column r at r * V or r * M).
+enum { MODE_JT = 0, MODE_J = 1, MODE_COUNT = 2, MODE_FROB = 3, MODE_COV = 4, MODE_JT4 = 5, MODE_J4 = 6 };
+constexpr int STG_PER_WARP = 128;   // staged float4 per warp: 32 rows x (3 or 4)
 
 struct ApplyParams {
     const RowRec* rec;
@@ -54,6 +57,7 @@ struct ApplyParams {
     double* dsum;            // FROB: [n_items * 8]
     unsigned long long* icount;   // COUNT
     int trig_nq;             // sine-series Phi: coefficient groups of 4 per band
+    int64_t nvox, nrow;      // column lengths of the batch modes' blocks (V, M)
 };
 
 // Phi of the normalised detour v from the band data at shared address tb (table lookup or
@@ -104,13 +108,14 @@ __device__ __forceinline__ float detour_v64(const RowRec64& r, double ox, double
 // Resident CTAs per SM the register budget is sized for: the stable-detour table kernels fit
 // 64 registers without spilling (4 CTAs, 32 warps per SM); the others keep 80 (3 CTAs) and
 // the sharp-band ones 128 (2 CTAs).
-template <int DT, bool SHARP, int PHI>
+template <int MODE, int DT, bool SHARP, int PHI>
 constexpr int apply_min_blocks() {
-    return SHARP ? 2 : ((DT == FFT_DT_STABLE && PHI == PHI_TABLE) ? 4 : 3);
+    return (SHARP || MODE == MODE_JT4 || MODE == MODE_J4) ? 2
+                                                          : ((DT == FFT_DT_STABLE && PHI == PHI_TABLE) ? 4 : 3);
 }
 
 template <int MODE, int DT, bool GUARD, bool SHARP, int PHI>
-__global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI>())
+__global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHARP, PHI>())
     apply_kernel(const __grid_constant__ ApplyParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* s_tab = reinterpret_cast<float2*>(smem);
@@ -125,7 +130,9 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
     const float nm1 = (float)(P.n_tab - 1);
     const int nq = P.trig_nq;
     const int lx = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
-    float4* stg = s_stage + warp * 96;
+    constexpr bool BATCH = (MODE == MODE_JT4 || MODE == MODE_J4);
+    constexpr int SR = BATCH ? 4 : 3;   // staged float4 per row
+    float4* stg = s_stage + warp * STG_PER_WARP;
     const int n_units = P.n_items * APPLY_WARPS;
 
     for (;;) {
@@ -160,6 +167,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
 
         float acc[2][NX_LANE];
         float mv[2][NX_LANE];
+        float acc4[2][NX_LANE][4];   // batch modes only
+        float mv4[2][NX_LANE][4];
         double dacc = 0.0;
         unsigned long long cnt = 0, cnt_eval = 0;
 #pragma unroll
@@ -170,6 +179,13 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                 mv[s][t] = 0.0f;
                 if (MODE == MODE_J && ((vmask >> (4 * s + t)) & 1u))
                     mv[s][t] = __ldg(P.vin + vbase + (int64_t)(4 * s) * P.nx + t);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    acc4[s][t][r] = 0.0f;
+                    mv4[s][t][r] = 0.0f;
+                    if (MODE == MODE_J4 && ((vmask >> (4 * s + t)) & 1u))
+                        mv4[s][t][r] = __ldg(P.vin + (int64_t)r * P.nvox + vbase + (int64_t)(4 * s) * P.nx + t);
+                }
             }
 
         for (int64_t e0 = item.e0; e0 < item.e1; e0 += 32) {
@@ -188,6 +204,10 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                 float W = r.b.w;
                 if (MODE == MODE_JT) W *= __ldg(P.vin + p);
                 if (MODE == MODE_COV) W = fabsf(W) * (P.vin ? fabsf(__ldg(P.vin + p)) : 1.0f);
+                float4 W4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (MODE == MODE_JT4)
+                    W4 = make_float4(W * __ldg(P.vin + p), W * __ldg(P.vin + P.nrow + p),
+                                     W * __ldg(P.vin + 2 * P.nrow + p), W * __ldg(P.vin + 3 * P.nrow + p));
                 const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
                 // sub-brick centres relative to the pair midpoint (FP32; used by the bound only)
                 const float dx = fmaf((float)TX, hb, bc.org[0]) - r.a.x;
@@ -199,7 +219,8 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                 const float cy1 = fmaf(8.0f * wy + 5.5f, hb, dy);
                 const float hxx = 3.5f * hb, hyy = 1.5f * hb;
                 // rows with zero weight add exactly nothing to J^T: skip them
-                const bool live = (MODE != MODE_JT && MODE != MODE_COV) || (W != 0.0f);
+                const bool live = (MODE == MODE_JT4) ? (W4.x != 0.0f || W4.y != 0.0f || W4.z != 0.0f || W4.w != 0.0f)
+                                                     : ((MODE != MODE_JT && MODE != MODE_COV) || (W != 0.0f));
                 ok0 = live && sub_ok0 && box_may_touch(cx, cy0, cz, ex, ey, ez, hl, hxx, hyy, hyy);
                 ok1 = live && sub_ok1 && box_may_touch(cx, cy1, cz, ex, ey, ez, hl, hxx, hyy, hyy);
                 // sub-bricks whose voxels all satisfy |p| <= hl (between the transducer planes)
@@ -208,11 +229,12 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                 in0 = fabsf(fmaf(cy0, ey, pcx)) + pext <= hl;
                 in1 = fabsf(fmaf(cy1, ey, pcx)) + pext <= hl;
                 const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - (PHI == PHI_TABLE ? MAGIC_BITS_X8 : 0u);
-                stg[lane * 3 + 0] = base;
-                stg[lane * 3 + 1] = make_float4(hb * ex, hb * ey, hb * ez, base3);
+                stg[lane * SR + 0] = base;
+                stg[lane * SR + 1] = make_float4(hb * ex, hb * ey, hb * ez, base3);
+                if (MODE == MODE_JT4) stg[lane * SR + 3] = W4;
                 // planar pair (both transducers at one z): stepping along x changes only c3
                 const int planar = (ez == 0.0f) ? 1 : 0;
-                stg[lane * 3 + 2] = make_float4(W, __uint_as_float(tb), __int_as_float(p),
+                stg[lane * SR + 2] = make_float4(W, __uint_as_float(tb), __int_as_float(p),
                                                 __int_as_float(b | (bc.sharp << 8) | (planar << 9)));
             }
             const uint32_t m0 = __ballot_sync(0xffffffffu, ok0);
@@ -222,12 +244,15 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
             __syncwarp();
             uint32_t mm = m0 | m1;
             float mypart = 0.0f;
+            float mypart4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             while (mm) {
                 const int bit = __ffs(mm) - 1;
                 mm &= mm - 1;
-                const float4 A = stg[bit * 3 + 0];
-                const float4 B = stg[bit * 3 + 1];
-                const float4 C = stg[bit * 3 + 2];
+                const float4 A = stg[bit * SR + 0];
+                const float4 B = stg[bit * SR + 1];
+                const float4 C = stg[bit * SR + 2];
+                const float4 W4 = (MODE == MODE_JT4) ? stg[bit * SR + 3] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float Wr[4] = {W4.x, W4.y, W4.z, W4.w};
                 const float hx = B.x, hy = B.y, hz = B.z, W = C.x;
                 const float hl = 0.5f * (A.x - A.y);   // used by the textbook (NAIVE) detour only
                 const uint32_t tb = __float_as_uint(C.y);
@@ -238,6 +263,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                 // lane base (sub-brick 0, t = 0) in the pair frame: small offsets added to the
                 // tile origin's FP64-derived values
                 float part = 0.0f;
+                float part4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                 // The entry's evaluation, specialised for planar pairs (both transducers at one
                 // z: the axis has no z component, so h_z = 0 exactly and c1, c2 do not change
                 // along the lane's voxels or between the two sub-bricks).
@@ -307,6 +333,12 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
         const float val = phi_lookup(v, tb, nm1) * (is * ir);                                      \
         if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                                  \
         if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val), W, acc[s][t]);                          \
+        if (MODE == MODE_JT4) {                                                                    \
+            _Pragma("unroll") for (int r = 0; r < 4; ++r) acc4[s][t][r] = fmaf(val, Wr[r], acc4[s][t][r]); \
+        }                                                                                          \
+        if (MODE == MODE_J4) {                                                                     \
+            _Pragma("unroll") for (int r = 0; r < 4; ++r) part4[r] = fmaf(val, mv4[s][t][r], part4[r]); \
+        }                                                                                          \
         if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                      \
         if (MODE == MODE_FROB) {                                                                   \
             if ((vmask >> (4 * s + t)) & 1u) part = fmaf(val, val, part);                          \
@@ -319,6 +351,12 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
             const float val = ph[t] * ww[t];                                                       \
             if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                              \
             if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val), W, acc[s][t]);                      \
+            if (MODE == MODE_JT4) {                                                                \
+                _Pragma("unroll") for (int r = 0; r < 4; ++r) acc4[s][t][r] = fmaf(val, Wr[r], acc4[s][t][r]); \
+            }                                                                                      \
+            if (MODE == MODE_J4) {                                                                 \
+                _Pragma("unroll") for (int r = 0; r < 4; ++r) part4[r] = fmaf(val, mv4[s][t][r], part4[r]); \
+            }                                                                                      \
             if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                  \
             if (MODE == MODE_FROB) {                                                               \
                 if ((vmask >> (4 * s + t)) & 1u) part = fmaf(val, val, part);                      \
@@ -389,6 +427,14 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                             if (MODE == MODE_JT) acc[s][t] = fmaf(val2 - val1, W, acc[s][t]);
                             if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val2) - fabsf(val1), W, acc[s][t]);
                             if (MODE == MODE_J) part = fmaf(val2 - val1, mv[s][t], part);
+                            if (MODE == MODE_JT4) {
+#pragma unroll
+                                for (int r = 0; r < 4; ++r) acc4[s][t][r] = fmaf(val2 - val1, Wr[r], acc4[s][t][r]);
+                            }
+                            if (MODE == MODE_J4) {
+#pragma unroll
+                                for (int r = 0; r < 4; ++r) part4[r] = fmaf(val2 - val1, mv4[s][t][r], part4[r]);
+                            }
                             if (MODE == MODE_FROB) {
                                 if ((vmask >> (4 * s + t)) & 1u) part += val2 * val2 - val1 * val1;
                             }
@@ -399,9 +445,19 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                     part = warp_sum(part);
                     if (lane == bit) mypart = part * W;
                 }
+                if (MODE == MODE_J4) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float pr4 = warp_sum(part4[r]);
+                        if (lane == bit) mypart4[r] = pr4 * W;
+                    }
+                }
                 if (MODE == MODE_FROB) dacc += (double)part * (double)W * (double)W;
             }
             if (MODE == MODE_J && have) P.vout[e * 8 + region] = mypart;
+            if (MODE == MODE_J4 && have)
+                *reinterpret_cast<float4*>(P.vout + (e * 8 + region) * 4) =
+                    make_float4(mypart4[0], mypart4[1], mypart4[2], mypart4[3]);
             __syncwarp();
         }
 
@@ -417,6 +473,24 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<DT, SHARP, PHI
                     const int loc = ((ozi * TILE_Y) + oyi + 4 * s) * TILE_X + oxi;
                     float4 v4 = make_float4(acc[s][0], acc[s][1], acc[s][2], acc[s][3]);
                     *reinterpret_cast<float4*>(P.gpart + (int64_t)item.slot * TILE_VOX + loc) = v4;
+                }
+            }
+        }
+        if (MODE == MODE_JT4) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int loc = ((ozi * TILE_Y) + oyi + 4 * s) * TILE_X + oxi;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (item.slot < 0) {
+#pragma unroll
+                        for (int t = 0; t < NX_LANE; ++t)
+                            if ((vmask >> (4 * s + t)) & 1u)
+                                P.vout[(int64_t)r * P.nvox + vbase + (int64_t)(4 * s) * P.nx + t] = acc4[s][t][r];
+                    } else {
+                        float4 v4 = make_float4(acc4[s][0][r], acc4[s][1][r], acc4[s][2][r], acc4[s][3][r]);
+                        *reinterpret_cast<float4*>(P.gpart + ((int64_t)item.slot * 4 + r) * TILE_VOX + loc) = v4;
+                    }
                 }
             }
         }
@@ -459,6 +533,57 @@ __global__ void __launch_bounds__(256) j_reduce_kernel(const int64_t* __restrict
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) d[p] = (float)s;
+}
+
+// The four-column form of j_reduce_kernel: jpart4[(entry * 8 + region) * 4 + r]; the same lane
+// order, pairing and butterfly per column, d[r * M + p].
+__global__ void __launch_bounds__(256) j_reduce4_kernel(const int64_t* __restrict__ row_off,
+                                                        const int64_t* __restrict__ row_ent,
+                                                        const float* __restrict__ jpart4, int64_t M,
+                                                        float* __restrict__ d) {
+    const int lane = threadIdx.x & 31;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= M) return;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t j1 = row_off[p + 1];
+    for (int64_t j = row_off[p] + lane; j < j1; j += 32) {
+        const float4* q = reinterpret_cast<const float4*>(jpart4 + row_ent[j] * 32);
+        float4 g[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) g[k] = __ldg(q + k);
+        s[0] += (double)(((g[0].x + g[1].x) + (g[2].x + g[3].x)) + ((g[4].x + g[5].x) + (g[6].x + g[7].x)));
+        s[1] += (double)(((g[0].y + g[1].y) + (g[2].y + g[3].y)) + ((g[4].y + g[5].y) + (g[6].y + g[7].y)));
+        s[2] += (double)(((g[0].z + g[1].z) + (g[2].z + g[3].z)) + ((g[4].z + g[5].z) + (g[6].z + g[7].z)));
+        s[3] += (double)(((g[0].w + g[1].w) + (g[2].w + g[3].w)) + ((g[4].w + g[5].w) + (g[6].w + g[7].w)));
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        double v = s[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) d[(int64_t)r * M + p] = (float)v;
+    }
+}
+
+// The four-column form of jt_reduce_kernel: slot q of column r at gpart4[((s0 + q) * 4 + r)
+// * TILE_VOX + loc], g[r * V + v].
+__global__ void jt_reduce4_kernel(const int32_t* __restrict__ slot0, const int32_t* __restrict__ nslot,
+                                  const float* __restrict__ gpart4, int nx, int ny, int nz, int tiles_x,
+                                  int tiles_y, float* __restrict__ g) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t V = (int64_t)nx * ny * nz;
+    if (v >= V) return;
+    int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
+    int T = (k / TILE_Z * tiles_y + j / TILE_Y) * tiles_x + i / TILE_X;
+    int s0 = slot0[T];
+    if (s0 == -1) return;
+    int loc = ((k % TILE_Z) * TILE_Y + (j % TILE_Y)) * TILE_X + (i % TILE_X);
+    for (int r = 0; r < 4; ++r) {
+        float s = 0.0f;
+        if (s0 != -2)
+            for (int q = 0; q < nslot[T]; ++q) s += gpart4[((int64_t)(s0 + q) * 4 + r) * TILE_VOX + loc];
+        g[(int64_t)r * V + v] = s;
+    }
 }
 
 // g for voxels of tiles with several items (sum of slots in item order) or with none (0).
@@ -510,12 +635,14 @@ static ApplyParams make_params(fft_geom g) {
     P.dsum = nullptr;
     P.icount = nullptr;
     P.trig_nq = g->trig_nq;
+    P.nvox = g->V;
+    P.nrow = g->M;
     return P;
 }
 
 size_t apply_smem(fft_geom g) {
     size_t tab = ((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15;
-    return tab + (size_t)APPLY_WARPS * 96 * sizeof(float4);
+    return tab + (size_t)APPLY_WARPS * STG_PER_WARP * sizeof(float4);
 }
 
 template <int MODE, int DT, bool G, bool S, int PHI>
@@ -552,6 +679,11 @@ fft_status set_apply_attributes(fft_geom g) {
     if ((rc = set_attr_mode<MODE_J>(smem)) != FFT_OK) return rc;
     if ((rc = set_attr_mode<MODE_COUNT>(smem)) != FFT_OK) return rc;
     if ((rc = set_attr_mode<MODE_COV>(smem)) != FFT_OK) return rc;
+    // batch modes: stable detour only (other geometries apply the columns one by one)
+    if ((rc = set_attr_dt<MODE_JT4, FFT_DT_STABLE, PHI_TABLE>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_dt<MODE_JT4, FFT_DT_STABLE, PHI_TRIG>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_dt<MODE_J4, FFT_DT_STABLE, PHI_TABLE>(smem)) != FFT_OK) return rc;
+    if ((rc = set_attr_dt<MODE_J4, FFT_DT_STABLE, PHI_TRIG>(smem)) != FFT_OK) return rc;
     return set_attr_mode<MODE_FROB>(smem);
 }
 
@@ -598,6 +730,103 @@ static fft_status launch_mode(fft_geom g, const ApplyParams& P, cudaStream_t st)
 #undef FFT_LAUNCH_GS
 #undef FFT_LAUNCH
     FFT_CUDA(cudaGetLastError());
+    return FFT_OK;
+}
+
+// The four-column modes (stable detour only).
+template <int MODE>
+static fft_status launch_batch(fft_geom g, const ApplyParams& P, cudaStream_t st) {
+    const size_t smem = apply_smem(g);
+    const int ctas = g->apply_ctas;
+    FFT_CUDA(cudaMemsetAsync(g->counter, 0, sizeof(int32_t), st));
+    if (g->n_items == 0) return FFT_OK;
+#define FFT_LAUNCH(GV, SV, PV) apply_kernel<MODE, FFT_DT_STABLE, GV, SV, PV><<<ctas, APPLY_THREADS, smem, st>>>(P)
+#define FFT_LAUNCH_GS(PV)                                           \
+    do {                                                            \
+        if (g->guard) {                                             \
+            if (g->sharp) FFT_LAUNCH(true, true, PV);               \
+            else FFT_LAUNCH(true, false, PV);                       \
+        } else {                                                    \
+            if (g->sharp) FFT_LAUNCH(false, true, PV);              \
+            else FFT_LAUNCH(false, false, PV);                      \
+        }                                                           \
+    } while (0)
+    if (g->phi_kind == PHI_TRIG)
+        FFT_LAUNCH_GS(PHI_TRIG);
+    else
+        FFT_LAUNCH_GS(PHI_TABLE);
+#undef FFT_LAUNCH_GS
+#undef FFT_LAUNCH
+    FFT_CUDA(cudaGetLastError());
+    return FFT_OK;
+}
+
+static fft_status batch_scratch(fft_geom g) {
+    if (!g->jpart4) {
+        cudaError_t e = cudaMalloc(&g->jpart4, sizeof(float) * (size_t)(g->E > 0 ? g->E : 1) * 32);
+        if (e == cudaSuccess && g->n_slots > 0)
+            e = cudaMalloc(&g->gpart4, sizeof(float) * (size_t)g->n_slots * 4 * TILE_VOX);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(g->jpart4);
+            g->jpart4 = nullptr;
+            set_error("batch apply: cudaMalloc of the four-column scratch failed");
+            return FFT_ERR_OOM;
+        }
+        g->scratch_bytes += (int64_t)(sizeof(float) * ((size_t)g->E * 32 + (size_t)g->n_slots * 4 * TILE_VOX));
+    }
+    return FFT_OK;
+}
+
+// d[:, c] = J m[:, c] for n columns: groups of four with the batch kernel on stable-detour
+// geometries, single columns otherwise.
+fft_status launch_J_batch(fft_geom g, const float* m, int n, float* d, cudaStream_t st) {
+    int c = 0;
+    if (g->dt_mode == FFT_DT_STABLE && n >= 4) {
+        fft_status rc = batch_scratch(g);
+        if (rc != FFT_OK) return rc;
+        for (; c + 4 <= n; c += 4) {
+            ApplyParams P = make_params(g);
+            P.vin = m + (int64_t)c * g->V;
+            P.vout = g->jpart4;
+            if ((rc = launch_batch<MODE_J4>(g, P, st)) != FFT_OK) return rc;
+            if (g->M > 0) {
+                j_reduce4_kernel<<<(unsigned)ceil_div(g->M, 8), 256, 0, st>>>(g->row_off, g->row_ent, g->jpart4, g->M,
+                                                                              d + (int64_t)c * g->M);
+                FFT_CUDA(cudaGetLastError());
+            }
+        }
+    }
+    for (; c < n; ++c) {
+        fft_status rc = launch_J(g, m + (int64_t)c * g->V, d + (int64_t)c * g->M, st);
+        if (rc != FFT_OK) return rc;
+    }
+    return FFT_OK;
+}
+
+// g[:, c] = J^T d[:, c] for n columns (groups of four as above).
+fft_status launch_JT_batch(fft_geom g, const float* din, int n, float* gout, cudaStream_t st) {
+    int c = 0;
+    if (g->dt_mode == FFT_DT_STABLE && n >= 4) {
+        fft_status rc = batch_scratch(g);
+        if (rc != FFT_OK) return rc;
+        for (; c + 4 <= n; c += 4) {
+            ApplyParams P = make_params(g);
+            P.vin = din + (int64_t)c * g->M;
+            P.vout = gout + (int64_t)c * g->V;
+            P.gpart = g->gpart4;
+            if ((rc = launch_batch<MODE_JT4>(g, P, st)) != FFT_OK) return rc;
+            jt_reduce4_kernel<<<(unsigned)ceil_div(g->V, 256), 256, 0, st>>>(g->tile_slot0, g->tile_nslot, g->gpart4,
+                                                                          g->grid.nx, g->grid.ny, g->grid.nz,
+                                                                          g->tiles[0], g->tiles[1],
+                                                                          gout + (int64_t)c * g->V);
+            FFT_CUDA(cudaGetLastError());
+        }
+    }
+    for (; c < n; ++c) {
+        fft_status rc = launch_JT(g, din + (int64_t)c * g->M, gout + (int64_t)c * g->V, st);
+        if (rc != FFT_OK) return rc;
+    }
     return FFT_OK;
 }
 
@@ -697,6 +926,22 @@ extern "C" fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev,
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
     return launch_JT(g, d_dev, g_dev, (cudaStream_t)stream);
+}
+
+extern "C" fft_status fft_J_apply_batch(fft_geom g, const float* m_dev, int32_t n, float* d_dev, void* stream) {
+    FFT_ARG(g && m_dev && d_dev, "fft_J_apply_batch: null argument");
+    FFT_ARG(n >= 1, "fft_J_apply_batch: need n >= 1 columns");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    return launch_J_batch(g, m_dev, n, d_dev, (cudaStream_t)stream);
+}
+
+extern "C" fft_status fft_JT_apply_batch(fft_geom g, const float* d_dev, int32_t n, float* g_dev, void* stream) {
+    FFT_ARG(g && d_dev && g_dev, "fft_JT_apply_batch: null argument");
+    FFT_ARG(n >= 1, "fft_JT_apply_batch: need n >= 1 columns");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    return launch_JT_batch(g, d_dev, n, g_dev, (cudaStream_t)stream);
 }
 
 extern "C" fft_status fft_coverage(fft_geom g, const float* w_dev, float* cov_dev, void* stream) {

@@ -151,6 +151,8 @@ struct fft_geom_s {
     double* cg_dots = nullptr;           // [2 * DOT_BLOCKS] partial inner products
     int32_t* cg_status = nullptr;        // [1]
     float* vol = nullptr;                // [V] volume scratch of the 2-D apply (allocated on first use)
+    float* jpart4 = nullptr;             // [E * 8 * 4] J partials of the four-column apply (first use)
+    float* gpart4 = nullptr;             // [n_slots * 4 * TILE_VOX] J^T partials of the four-column apply
     double* cg_hist = nullptr;           // [cg_hist_cap]
     int32_t cg_hist_cap = 0;
     void* cg_graph = nullptr;            // cudaGraphExec_t of the iteration loop
@@ -162,6 +164,8 @@ namespace fftgb {
 // Launch helpers implemented in fft_apply.cu (used by CG and PSF).
 fft_status launch_J(fft_geom g, const float* m, float* d, cudaStream_t st);
 fft_status launch_JT(fft_geom g, const float* din, float* gout, cudaStream_t st);
+fft_status launch_J_batch(fft_geom g, const float* m, int n, float* d, cudaStream_t st);
+fft_status launch_JT_batch(fft_geom g, const float* din, int n, float* gout, cudaStream_t st);
 fft_status launch_JT_rows(fft_geom g, const float* din, float* gout, cudaStream_t st);
 fft_status check_device(int dev);
 fft_status count_support(fft_geom g, int64_t* support, int64_t* evaluated);

@@ -182,7 +182,7 @@ void free_geom(fft_geom g) {
     void* ptrs[] = {g->d_band, g->rec, g->rec64, g->row_band, g->tab, g->tile_off, g->tile_rows, g->ebase, g->ebase3,
                     g->row_off, g->row_ent, g->items, g->tile_slot0, g->tile_nslot, g->jpart,
                     g->gpart, g->counter, g->cg_r, g->cg_q, g->cg_s, g->cg_p, g->cg_d, g->cg_m,
-                    g->cg_scal, g->cg_dots, g->cg_status, g->cg_hist, g->vol};
+                    g->cg_scal, g->cg_dots, g->cg_status, g->cg_hist, g->vol, g->jpart4, g->gpart4};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->cg_graph) cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph);
@@ -247,7 +247,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
         int optin = 0;
         FFT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         size_t need = (((size_t)n_tables * n_tab * sizeof(float2) + 15) & ~(size_t)15) +
-                      (size_t)APPLY_WARPS * 96 * sizeof(float4);
+                      (size_t)APPLY_WARPS * 128 * sizeof(float4);
         if (need > (size_t)optin) {
             set_error("fft_geom_create: the tables (n_tables x n_samples x 8 bytes) do not fit in shared memory");
             return FFT_ERR_ARG;

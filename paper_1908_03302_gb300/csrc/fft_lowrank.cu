@@ -6,7 +6,7 @@
 // Review 53, 2011, Algorithms 4.4 and 5.3):
 //   Y = H Omega;  n_power times { Q = orth(Y); Y = H Q };  Q = orth(Y);
 //   T = Q^T (H Q) = U diag(l) U^T;  V_k = Q U_k (largest k).
-// H is applied column by column with the J and J^T kernels. orth is SVQB (Stathopoulos and
+// H is applied four columns at a time with the batch J and J^T kernels. orth is SVQB (Stathopoulos and
 // Wu, SIAM J. Sci. Comput. 23, 2002) applied three times: with the Gram matrix G = Y^T Y
 // (accumulated in FP64) and its eigendecomposition G = U D U^T, Q = Y U D^{-1/2}, where
 // directions with D below 1e-12 max D (numerically in the null space: a block wider than the
@@ -229,12 +229,14 @@ fft_status orthonormalise(LowrankWork& W, float* Y, int n, float* Q) {
     return FFT_OK;
 }
 
-// Y = J^T (J X) for the n columns of X (unscaled by sigma).
+// Y = J^T (J X) for the n columns of X (unscaled by sigma), four columns per application of
+// the batch kernels; tmpM holds four columns of length M.
 fft_status apply_H(fft_geom g, const float* X, int n, float* Y, float* tmpM, cudaStream_t st) {
-    for (int j = 0; j < n; ++j) {
-        fft_status rc = launch_J(g, X + (int64_t)j * g->V, tmpM, st);
+    for (int j = 0; j < n; j += 4) {
+        const int c = std::min(4, n - j);
+        fft_status rc = launch_J_batch(g, X + (int64_t)j * g->V, c, tmpM, st);
         if (rc != FFT_OK) return rc;
-        if ((rc = launch_JT(g, tmpM, Y + (int64_t)j * g->V, st)) != FFT_OK) return rc;
+        if ((rc = launch_JT_batch(g, tmpM, c, Y + (int64_t)j * g->V, st)) != FFT_OK) return rc;
     }
     return FFT_OK;
 }
@@ -262,7 +264,7 @@ extern "C" fft_status fft_hessian_lowrank(fft_geom g, const float* omega_dev, in
     const size_t blk = sizeof(float) * (size_t)g->V * ell;
     cudaError_t e = cudaMalloc(&Y, blk);
     if (e == cudaSuccess) e = cudaMalloc(&Q, blk);
-    if (e == cudaSuccess) e = cudaMalloc(&tmpM, sizeof(float) * (size_t)g->M);
+    if (e == cudaSuccess) e = cudaMalloc(&tmpM, sizeof(float) * (size_t)g->M * 4);
     if (e == cudaSuccess) e = cudaMalloc(&W.part, sizeof(double) * (size_t)W.chunks * MAX_ELL * MAX_ELL);
     if (e == cudaSuccess) e = cudaMalloc(&W.wmat, sizeof(float) * MAX_ELL * MAX_ELL);
     if (e != cudaSuccess) {
