@@ -451,7 +451,7 @@ def main():
     ap.add_argument("--phi", default="table", choices=["table", "trig"],
                     help="Phi representation: sampled table (default) or sine series")
     ap.add_argument("--trig-terms", type=int, default=0, help="sine-series terms (0: automatic)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch"],
                     help="apply: only build the geometry and run --steps J^T and J applications "
                          "(a short program for ncu captures; prints timings, not the bench line)")
     args = ap.parse_args()
@@ -519,6 +519,26 @@ def main():
                 print(json.dumps({"apply": i, "ms_JT": a.elapsed_time(b), "ms_J": c.elapsed_time(e),
                                   "support": support, "evaluated": int(info.evaluated_evals),
                                   "entries": int(info.n_entries), "items": int(info.n_items)}), flush=True)
+        return 0
+    if args.mode == "batch":
+        # four-column J^T and J (one group), the Hessian columns of the low-rank solver
+        D4 = torch.randn((4, geo.M), device=dev, dtype=torch.float32) * 1e-8
+        M4 = torch.randn((4, geo.V), device=dev, dtype=torch.float32)
+        G4 = torch.empty((4, geo.V), device=dev, dtype=torch.float32)
+        Q4 = torch.empty((4, geo.M), device=dev, dtype=torch.float32)
+        for i in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            geo.JT_batch(D4, out=G4)
+            b.record(stream)
+            c.record(stream)
+            geo.J_batch(M4, out=Q4)
+            e.record(stream)
+            torch.cuda.synchronize()
+            if rank == 0:
+                print(json.dumps({"batch": i, "columns": 4, "ms_JT4": a.elapsed_time(b), "ms_J4": c.elapsed_time(e),
+                                  "support": support}), flush=True)
         return 0
 
     for _ in range(args.warmup):
