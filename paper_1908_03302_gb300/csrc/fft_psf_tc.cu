@@ -95,6 +95,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// GUARD: some voxel centre lies on a transducer (the geometry's flag): the guarded detour.
+template <bool GUARD>
 __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_constant__ PsfTcParams P) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ TcShared S;
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                           \
         }                                                                                        \
         float is, ir;                                                                            \
-        const float v = detour_v<FFT_DT_STABLE, true, INNER_V>(pst, prt, q2, 0.0f, is, ir);      \
+        const float v = detour_v<FFT_DT_STABLE, GUARD, INNER_V>(pst, prt, q2, 0.0f, is, ir);     \
         vals[rr][t] = phi_lookup(v, tb, nm1) * (is * ir) * C4.x;                                 \
     }
                             if (tbf & 1u) {
@@ -537,9 +539,13 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
         return FFT_ERR_ARG;
     }
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(psf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(g->guard ? psf_tc_kernel<true> : psf_tc_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        psf_tc_kernel<<<sms, TC_THREADS, smem, st>>>(P);
+        if (g->guard)
+            psf_tc_kernel<true><<<sms, TC_THREADS, smem, st>>>(P);
+        else
+            psf_tc_kernel<false><<<sms, TC_THREADS, smem, st>>>(P);
         e = cudaGetLastError();
     }
     int32_t status = 0;

@@ -70,3 +70,25 @@ def test_psf_tc_ragged_tiny(fg_tiny=None):
     for s in range(2):
         for k in range(3):
             assert rel_l2(tc[s, k], ref[s, k]) <= 1e-2
+
+
+def test_psf_tc_transducer_on_a_voxel_centre():
+    # the guarded tensor-core kernel: a transducer exactly on a voxel centre of a ragged grid
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1908_03302_gb300 as fg
+    w = wl.tiny()
+    g = w.grid
+    tx = w.tx.copy()
+    tx[0] = [g.origin[0] + 3 * g.h, g.origin[1] + 5 * g.h, g.origin[2] + 2 * g.h]
+    geo = fg.Geometry(tx, w.row_pairs(), g, w.c0, [fg.Table(1e6, 0.3e6, 4096, 3e-6)])
+    og = oracle.Geometry(tx, w.row_pairs(), None, [oracle.phi_table_gauss(1e6, 0.3e6, 4096, 3e-6)], [3e-6], g, w.c0)
+    spikes = np.array([(2 * g.ny + 5) * g.nx + 4, 611, 950], dtype=np.int64)   # one next to the transducer
+    subsets = [np.arange(0, og.M, 2, dtype=np.int32), np.arange(og.M, dtype=np.int32)]
+    ref = og.psf(spikes, subsets)
+    tc = to_np(geo.psf_batch(spikes, subsets, mode=1))
+    fp = to_np(geo.psf_batch(spikes, subsets, mode=0))
+    for s in range(2):
+        for k in range(3):
+            assert rel_l2(fp[s, k], ref[s, k]) <= 1e-5
+            assert rel_l2(tc[s, k], ref[s, k]) <= 1e-2
