@@ -46,7 +46,7 @@ FP32_LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) of one J^T apply-kernel launch on this workload, from the ncu
 # capture summarised in profiles/apply_kernel_ring256.md; None until captured for the
 # current kernel.
-APPLY_TRAFFIC_BYTES = 126160128   # 102703616 read + 23456512 written (ncu, one J^T launch on ring256)
+APPLY_TRAFFIC_BYTES = 125214720   # 101971712 read + 23243008 written (ncu, one J^T launch on ring256)
 
 
 def peaks():
