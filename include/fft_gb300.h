@@ -93,8 +93,8 @@ fft_status fft_table_build(const fft_spectrum* spec, int32_t n_samples, double d
 void fft_table_destroy(fft_table t);
 
 /*
- * fft_trig_build - Phi as a short sine series, the form Sec. II-C stores ("coefficients and
- * arguments" of the trigonometric terms of Eq. Kernel_freq) in place of a sampled table:
+ * fft_trig_build - Phi as a short sine series, the form Sec. II-C keeps (amplitudes and
+ * frequencies of the sine terms of Eq. Kernel_freq) in place of a sampled table:
  *   Phi(dt) = sum_{j=1..n} a_j sin(j dw dt),  0 for dt <= 0 or dt >= dt_max,
  *   a_j = dw w_j^3 W(w_j) / int_0^inf w^2 W(w) dw,  w_j = j dw,
  * i.e. both integrals by the rectangle rule on equally spaced nodes (the denominator in

@@ -145,7 +145,7 @@ int oracle_phi_table(int kind, double fc, double fsig, const double* om, const d
  *   Phi(dt) = sum_j a_j sin(w_j dt),   a_j = dw w_j^3 W(w_j) / int_0^inf w^2 W(w) dw,
  * the denominator by the composite Simpson rule of oracle_phi_table (n_quad intervals).
  * The rule is exact up to aliasing from the period T = 2 pi / dw of the series and the
- * truncation of the terms (reading of the paper's "very few terms"):
+ * truncation of the terms (the paper says a small number of terms suffices, not which):
  *   T = max(2 dt_max, dt_max + 6.5 / s)   (Phi decays like exp(-s^2 t^2 / 2): images of
  *                                          Phi shifted by T are negligible on [0, dt_max]),
  *   n = ceil((w0 + 5.5 s) / dw)           (W < 3e-7 beyond; series error < 2e-8 of max |Phi|),

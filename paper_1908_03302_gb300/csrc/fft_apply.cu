@@ -1,5 +1,5 @@
-// J m and J^T d, rebuilt on the fly (Sec. II-C: "the elements of F are computed on the fly
-// through the matrix-vector products"), tile-centric on sm_103a.
+// J m and J^T d with every entry of J recomputed inside each product instead of stored
+// (Sec. II-C), tile-centric on sm_103a.
 //
 // Work decomposition
 //   * The voxel grid is cut into 16 x 16 x 8 tiles. Each tile has a list of candidate rows

@@ -171,8 +171,8 @@ extern "C" void fft_table_destroy(fft_table t) {
     delete t;
 }
 
-// Sine-series form of Phi (Sec. II-C: coefficients and arguments of the trigonometric terms
-// of Eq. Kernel_freq). Both integrals by the rectangle rule on the nodes w_j = j dw; for the
+// Sine-series form of Phi (Sec. II-C stores Phi through the amplitudes and frequencies of
+// the sine terms of Eq. Kernel_freq). Both integrals by the rectangle rule on the nodes w_j = j dw; for the
 // even Gaussian W the denominator is int_0^inf w^2 W dw = sqrt(2 pi) s (w0^2 + s^2).
 extern "C" fft_status fft_trig_build(const fft_spectrum* spec, double dt_max, int32_t n_terms, double* coef_out,
                                      double* dw_out, int32_t* n_terms_out, fft_table* out) {

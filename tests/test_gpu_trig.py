@@ -1,5 +1,5 @@
-"""Parity of the sine-series Phi path (Sec. II-C: Phi stored as the coefficients and arguments
-of its sine terms, evaluated on the fly) with the FP64 oracle's series, through the C ABI.
+"""Parity of the sine-series Phi path (Sec. II-C: Phi stored as the amplitudes and frequencies
+of its sine terms, evaluated inside every product) with the FP64 oracle's series, through the C ABI.
 
 Tolerances as for the table path: J and J^T <= 1e-5 relative L2, CG model <= 1e-4. The FP32
 Clenshaw recurrence is good to a few 1e-6 of max |Phi| (it amplifies the rounding of cos x by

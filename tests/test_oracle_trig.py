@@ -1,5 +1,5 @@
 """Pins for the oracle's sine-series form of Phi (Sec. II-C: the operator is stored as the
-coefficients and arguments of the sine terms of Eq. Kernel_freq) and for the geometry that
+amplitudes and frequencies of the sine terms of Eq. Kernel_freq) and for the geometry that
 uses it.
 
 * the series against the closed form of Phi for the Gaussian power spectrum, for the
@@ -25,7 +25,7 @@ SPECTRA = [(1.0e6, 0.3e6, 3.0e-6), (1.0e6, 0.4e6, 3.0e-6), (0.6e6, 0.2e6, 5.0e-6
 @pytest.mark.parametrize("fc,fs,dtm", SPECTRA)
 def test_series_matches_closed_form(fc, fs, dtm):
     a, dw = oracle.trig_coefs(fc, fs, dtm)
-    assert 15 <= len(a) <= 30             # "very few terms"
+    assert 15 <= len(a) <= 30             # a short series
     t = np.linspace(0.0, dtm, 2001)[1:-1]
     ph = np.array([oracle.phi_trig(a, dw, dtm, x) for x in t])
     ex = cf.phi_gauss_closed(t, fc, fs)
