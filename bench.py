@@ -242,9 +242,19 @@ def run_psf(args, ws, rank, local):
     for _ in range(args.warmup):
         geo.psf_batch(spikes, subsets, mode=1, out=out_tc)
     tc_ms = [timed(lambda: geo.psf_batch(spikes, subsets, mode=1, out=out_tc)) for _ in range(args.steps)]
+    # tensor-core work of one batch: MMA flops (2 x generated J entries x MMA width) against the
+    # measured sustained BF16 rate, and the rate at which J entries are generated
+    pk, pk_kind = peaks()
+    mma_flops = float(geo.info().psf_tc_mma_flops)
+    tc_s = statistics.mean(tc_ms) * 1e-3
+    peak_tc = float(pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops") or 1700.0)
+    tensor = {"mma_tflops": mma_flops / tc_s / 1e12, "peak_tflops": peak_tc,
+              "peak_basis": f"bf16 sustained ({pk_kind})", "frac": mma_flops / tc_s / 1e12 / peak_tc,
+              "mma_flops_per_batch": mma_flops}
     if args.psf_tc_only:
         if rank == 0:
-            print(json.dumps({"psf_tc_ms": tc_ms, "geometry": w.name, "spikes": len(spikes)}), flush=True)
+            print(json.dumps({"psf_tc_ms": tc_ms, "geometry": w.name, "spikes": len(spikes), "tensor": tensor}),
+                  flush=True)
         return 0
     # FP32 path on a slice of the spikes (same per-PSF cost), scaled to the whole batch
     k32 = min(len(spikes), args.psf_fp32_spikes)
@@ -303,6 +313,7 @@ def run_psf(args, ws, rank, local):
                    "support_evals_per_apply": int(info.support_evals)},
         "fp32_path_ms_per_batch": fp_full_ms, "fp32_path_measured": f"{k32} spikes x 3 subsets, scaled",
         "speedup_tc_vs_fp32": fp_full_ms / tc_avg,
+        "tensor": tensor,
         "tc_vs_fp32_rel_l2_max": max(diff) if diff else None,
         "err_vs_fp64_oracle": {"tc_rel_l2_max": max(errs_tc), "fp32_rel_l2_max": max(errs_fp),
                                "sample": "2 spikes x subsets {64, 256}, <=256 voxels within 20 of the spike"}

@@ -152,6 +152,8 @@ typedef struct {
     int32_t dt_mode;
     int64_t evaluated_evals; /* (row, voxel) evaluations one apply performs after culling */
     int32_t phi_terms;       /* 0: sampled tables; else the largest sine-series length */
+    double psf_tc_mma_flops; /* tensor-core MMA flops of the last fft_psf_batch call in mode 1:
+                                2 x 128 x 32 x N per chunk of generated J tile, N the MMA width */
 } fft_geom_info_t;
 fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info);
 

@@ -564,5 +564,6 @@ extern "C" fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info) {
     info->scratch_bytes = g->scratch_bytes;
     info->dt_mode = g->dt_mode;
     info->phi_terms = g->trig_terms;
+    info->psf_tc_mma_flops = g->psf_tc_mma_flops;
     return FFT_OK;
 }

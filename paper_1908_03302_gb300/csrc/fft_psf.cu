@@ -119,6 +119,7 @@ namespace {
 fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, const int32_t* subset_off,
                        int32_t n_subsets, const int32_t* d_rows, float* out_dev, cudaStream_t st) {
     const int max_cols = psf_tc_max_cols(g);
+    g->psf_tc_mma_flops = 0.0;
     if (max_cols < n_subsets) {
         set_error("fft_psf_batch: the tensor-core tiles do not fit in shared memory with these tables");
         return FFT_ERR_ARG;

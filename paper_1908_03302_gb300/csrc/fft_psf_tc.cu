@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "fft_common.cuh"
@@ -72,6 +73,7 @@ struct PsfTcParams {
     float* out;                // Y as out[j * V + v]
     int64_t V;
     int32_t* status;
+    unsigned long long* chunks;   // chunks (128 x 32 A tiles) issued, summed over CTAs
 };
 
 struct TcShared {
@@ -432,6 +434,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)P.tmem_cols);
+    if (tid == 0 && chunk > 0) atomicAdd(P.chunks, (unsigned long long)chunk);
 }
 
 }  // namespace
@@ -489,10 +492,10 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
 
     int32_t *d_units = nullptr, *d_ctr = nullptr;
     FFT_CUDA(cudaMalloc(&d_units, sizeof(int32_t) * units.size()));
-    cudaError_t e = cudaMalloc(&d_ctr, 2 * sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&d_ctr, 4 * sizeof(int32_t));   // counter, status, 64-bit chunk count
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_units, units.data(), sizeof(int32_t) * units.size(),
                                               cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, 4 * sizeof(int32_t), st);
 
     PsfTcParams P;
     P.rec = g->rec;
@@ -525,6 +528,7 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     P.out = out;
     P.V = g->V;
     P.status = d_ctr + 1;
+    P.chunks = reinterpret_cast<unsigned long long*>(d_ctr + 2);
 
     // at least 120 KB so that only one CTA (which holds TMEM for the whole launch) fits on an SM
     const size_t smem = std::max<size_t>(120 * 1024, psf_tc_smem(g, P.b_rows) - sizeof(TcShared) - 1024);
@@ -548,9 +552,14 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
             psf_tc_kernel<false><<<sms, TC_THREADS, smem, st>>>(P);
         e = cudaGetLastError();
     }
-    int32_t status = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_ctr + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    int32_t hs[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, d_ctr, sizeof(hs), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    const int32_t status = hs[1];
+    unsigned long long nch = 0;
+    memcpy(&nch, hs + 2, sizeof(nch));
+    // MMA work of this launch: every chunk multiplies a 128 x 32 BF16 tile by 32 x cols
+    g->psf_tc_mma_flops += 2.0 * 128.0 * KC * (double)cols * (double)nch;
     cudaFree(d_units);
     cudaFree(d_ctr);
     if (e != cudaSuccess) return cuda_fail(e, "psf tensor-core path");
