@@ -300,14 +300,14 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHAR
             is = 1.0f;                                                                             \
             ir = w;                                                                                \
         } else {                                                                                   \
-            const float pst = fmaf(ft, hx, psb);                                                   \
-            const float prt = fmaf(ft, hx, prb);                                                   \
-            const float c3t = fmaf(ft, hy, c3);                                                    \
+            const float pst = (t == 0 ? psb : fmaf(ft, hx, psb));                                  \
+            const float prt = (t == 0 ? prb : fmaf(ft, hx, prb));                                  \
+            const float c3t = (t == 0 ? c3 : fmaf(ft, hy, c3));                                    \
             float q2;                                                                              \
             if (PLANAR_V) {                                                                        \
                 q2 = fmaf(c3t, c3t, c12sq);                                                        \
             } else {                                                                               \
-                const float c2t = fmaf(-ft, hz, c2);                                               \
+                const float c2t = (t == 0 ? c2 : fmaf(-ft, hz, c2));                               \
                 q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                         \
             }                                                                                      \
             if (SHARP) {                                                                           \

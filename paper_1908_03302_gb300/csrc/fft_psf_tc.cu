@@ -301,13 +301,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
 #define FFT_TC_RUN(INNER_V, PLANAR_V)                                                              \
     _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                        \
         const float ft = (float)t;                                                               \
-        const float pst = fmaf(ft, hx, psb), prt = fmaf(ft, hx, prb);                            \
-        const float c3t = fmaf(ft, hy, c3);                                                      \
+        const float pst = (t == 0 ? psb : fmaf(ft, hx, psb)), prt = (t == 0 ? prb : fmaf(ft, hx, prb)); \
+        const float c3t = (t == 0 ? c3 : fmaf(ft, hy, c3));                                        \
         float q2;                                                                                \
         if (PLANAR_V) {                                                                          \
             q2 = fmaf(c3t, c3t, c12sq);                                                          \
         } else {                                                                                 \
-            const float c2t = fmaf(-ft, hz, c2);                                                 \
+            const float c2t = (t == 0 ? c2 : fmaf(-ft, hz, c2));                                   \
             q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                           \
         }                                                                                        \
         float is, ir;                                                                            \
