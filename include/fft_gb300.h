@@ -157,6 +157,26 @@ typedef struct {
 } fft_geom_info_t;
 fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info);
 
+/* Result of fft_geom_autotune. */
+typedef struct {
+    int32_t items_per_cta; /* chosen work-item granularity (items per persistent CTA) */
+    int32_t ctas_per_sm;   /* chosen persistent CTAs per SM of the J / J^T kernels */
+    double ms_J, ms_JT;    /* their measured times with the chosen decomposition */
+    int32_t n_tried;       /* candidates timed */
+} fft_tune_info_t;
+
+/*
+ * fft_geom_autotune - pick the work decomposition of J and J^T for this geometry by timing
+ * them on the device: a tile's candidate rows are cut into work items sized for 4, 8, 16, 32,
+ * 64 or 128 items per persistent CTA (at least 64 rows each), with the most CTAs per SM that
+ * fit or one fewer; each of the twelve candidates runs J^T and J once untimed and once timed
+ * (CUDA events on `stream`),
+ * and the fastest is kept (results do not depend on it beyond rounding of the split J^T
+ * sums). Synchronous; allocates test vectors for the duration of the call; invalidates a
+ * captured CG loop (the next fft_cg_solve captures again). info may be NULL.
+ */
+fft_status fft_geom_autotune(fft_geom g, void* stream, fft_tune_info_t* info);
+
 /*
  * fft_J_apply - d = J m (Eq. forward_compact; m in m/s, d in s).
  *   m_dev  device float32[V]; d_dev device float32[M] (written entirely). No aliasing.

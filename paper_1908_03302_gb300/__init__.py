@@ -172,6 +172,14 @@ class Geometry:
         check(_lib.load().fft_geom_info(self.handle, ctypes.byref(out)))
         return out
 
+    def autotune(self, stream=None) -> dict:
+        """Time J and J^T for twelve work decompositions (items per CTA x CTAs per SM) and keep
+        the fastest (fft_geom_autotune)."""
+        out = _lib.fft_tune_info_t()
+        check(_lib.load().fft_geom_autotune(self.handle, _stream_handle(stream), ctypes.byref(out)))
+        return {"items_per_cta": out.items_per_cta, "ctas_per_sm": out.ctas_per_sm, "ms_J": out.ms_J,
+                "ms_JT": out.ms_JT, "candidates": out.n_tried}
+
     @property
     def support_evals(self) -> int:
         return int(self.info().support_evals)

@@ -51,6 +51,11 @@ class fft_grid(ctypes.Structure):
                 ("h", ctypes.c_double), ("origin", ctypes.c_double * 3)]
 
 
+class fft_tune_info_t(ctypes.Structure):
+    _fields_ = [("items_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("ms_J", ctypes.c_double),
+                ("ms_JT", ctypes.c_double), ("n_tried", ctypes.c_int32)]
+
+
 class fft_geom_info_t(ctypes.Structure):
     _fields_ = [("n_rows", ctypes.c_int64), ("n_vox", ctypes.c_int64), ("n_entries", ctypes.c_int64),
                 ("n_items", ctypes.c_int64), ("support_evals", ctypes.c_int64),
@@ -69,6 +74,7 @@ SIGNATURES = {
                                        _I32, ctypes.POINTER(_VP)]),
     "fft_geom_destroy": (None, [_VP]),
     "fft_geom_info": (ctypes.c_int, [_VP, ctypes.POINTER(fft_geom_info_t)]),
+    "fft_geom_autotune": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(fft_tune_info_t)]),
     "fft_J_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_JT_apply": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "fft_coverage": (ctypes.c_int, [_VP, _VP, _VP, _VP]),

@@ -41,6 +41,7 @@ constexpr int APPLY_THREADS = APPLY_WARPS * 32;
 constexpr int NX_LANE = 4;             // voxels per lane per sub-brick (along x)
 constexpr int SUBS_PER_WARP = 2;
 constexpr int MAX_BANDS = 8;
+constexpr int DEFAULT_ITEMS_PER_CTA = 8;   // work items per persistent CTA before tuning
 constexpr float CULL_MARGIN = 2e-3f;   // in units of the band's maximum detour
 
 // Per-row record, lengths in units of the row's band maximum detour U_b = c0 * dt_max_b.
@@ -140,7 +141,8 @@ struct fft_geom_s {
     int64_t evaluated = 0;
     double frob2 = -1.0;
     int64_t scratch_bytes = 0;
-    int apply_ctas = 0;
+    int apply_ctas = 0;                  // persistent grid of the apply kernels
+    int items_per_cta = 0;               // work-item granularity (autotuned or the default)
     // CG workspace (allocated on first use)
     float* cg_r = nullptr;               // [M] residual d - J m
     float* cg_q = nullptr;               // [M] J p
@@ -166,6 +168,7 @@ namespace fftgb {
 fft_status launch_J(fft_geom g, const float* m, float* d, cudaStream_t st);
 fft_status launch_JT(fft_geom g, const float* din, float* gout, cudaStream_t st);
 fft_status launch_J_batch(fft_geom g, const float* m, int n, float* d, cudaStream_t st);
+fft_status build_items(fft_geom g, const std::vector<int64_t>& toff, int items_per_cta);
 fft_status launch_JT_batch(fft_geom g, const float* din, int n, float* gout, cudaStream_t st);
 fft_status launch_JT_rows(fft_geom g, const float* din, float* gout, cudaStream_t st);
 fft_status check_device(int dev);

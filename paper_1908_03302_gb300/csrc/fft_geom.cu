@@ -194,6 +194,76 @@ void free_geom(fft_geom g) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Work items: a tile's candidate rows in ranges of at most ch rows, ch chosen so that each
+// persistent CTA sees about items_per_cta items (at least 64 rows, a multiple of 32); tiles
+// split over several items write J^T partial slots. Heaviest items first. Replaces the
+// geometry's previous items, slots and partial buffers (the J partials do not depend on them).
+fft_status build_items(fft_geom g, const std::vector<int64_t>& toff, int items_per_cta) {
+    const int64_t target = (int64_t)items_per_cta * g->apply_ctas;
+    int64_t ch = std::max<int64_t>(64, ceil_div(std::max<int64_t>(g->E, 1), std::max<int64_t>(target, 1)));
+    ch = ceil_div(ch, 32) * 32;
+    std::vector<Item> items;
+    std::vector<int32_t> slot0(g->n_tiles, -2), nslot(g->n_tiles, 0);
+    int32_t slots = 0;
+    for (int64_t T = 0; T < g->n_tiles; ++T) {
+        const int64_t n = toff[T + 1] - toff[T];
+        if (n == 0) continue;
+        const int64_t k = ceil_div(n, ch);
+        if (k == 1) {
+            items.push_back(Item{(int32_t)T, -1, toff[T], toff[T + 1]});
+            slot0[T] = -1;
+        } else {
+            slot0[T] = slots;
+            nslot[T] = (int32_t)k;
+            for (int64_t q = 0; q < k; ++q) {
+                const int64_t a = toff[T] + q * ch, b = std::min(toff[T + 1], a + ch);
+                items.push_back(Item{(int32_t)T, slots + (int32_t)q, a, b});
+            }
+            slots += (int32_t)k;
+        }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const Item& x, const Item& y) { return (x.e1 - x.e0) > (y.e1 - y.e0); });
+    if (g->items) {   // the buffers below are replaced: take them out of the scratch count
+        g->scratch_bytes -= (int64_t)(sizeof(Item) * g->n_items + 2 * sizeof(int32_t) * g->n_tiles +
+                                      sizeof(float) * (size_t)g->n_slots * TILE_VOX);
+        if (g->jpart4)
+            g->scratch_bytes -= (int64_t)(sizeof(float) * ((size_t)g->E * 32 + (size_t)g->n_slots * 4 * TILE_VOX));
+    }
+    void* old[] = {g->items, g->tile_slot0, g->tile_nslot, g->gpart, g->gpart4};
+    for (void* q : old)
+        if (q) cudaFree(q);
+    g->items = nullptr;
+    g->tile_slot0 = g->tile_nslot = nullptr;
+    g->gpart = g->gpart4 = nullptr;
+    if (g->jpart4) {   // the four-column scratch is rebuilt with the new slot count on first use
+        cudaFree(g->jpart4);
+        g->jpart4 = nullptr;
+    }
+    g->n_items = (int32_t)items.size();
+    g->n_slots = slots;
+    g->items_per_cta = items_per_cta;
+    fft_status rc;
+    if ((rc = dmalloc(g, &g->items, items.size())) != FFT_OK) return rc;
+    if ((rc = dmalloc(g, &g->tile_slot0, g->n_tiles)) != FFT_OK) return rc;
+    if ((rc = dmalloc(g, &g->tile_nslot, g->n_tiles)) != FFT_OK) return rc;
+    if ((rc = dmalloc(g, &g->gpart, (size_t)slots * TILE_VOX)) != FFT_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!items.empty()) e = cudaMemcpy(g->items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->tile_slot0, slot0.data(), sizeof(int32_t) * g->n_tiles, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->tile_nslot, nslot.data(), sizeof(int32_t) * g->n_tiles, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "work items");
+    // a captured CG loop holds the old item list: capture again on the next solve
+    if (g->cg_graph) {
+        cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph);
+        g->cg_graph = nullptr;
+        g->cg_graph_iters = -1;
+    }
+    return FFT_OK;
+}
+
 }  // namespace fftgb
 
 using namespace fftgb;
@@ -494,45 +564,9 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     // ---- work items
     GEOM_TRY(set_apply_attributes(g));
     g->apply_ctas = apply_occupancy(g);
-    {
-        const int64_t target = 8 * (int64_t)g->apply_ctas;
-        int64_t ch = std::max<int64_t>(64, ceil_div(std::max<int64_t>(g->E, 1), target));
-        ch = ceil_div(ch, 32) * 32;
-        std::vector<Item> items;
-        std::vector<int32_t> slot0(g->n_tiles, -2), nslot(g->n_tiles, 0);
-        int32_t slots = 0;
-        for (int64_t T = 0; T < g->n_tiles; ++T) {
-            int64_t n = tcnt[T];
-            if (n == 0) continue;
-            int64_t k = ceil_div(n, ch);
-            if (k == 1) {
-                items.push_back(Item{(int32_t)T, -1, toff[T], toff[T + 1]});
-                slot0[T] = -1;
-            } else {
-                slot0[T] = slots;
-                nslot[T] = (int32_t)k;
-                for (int64_t q = 0; q < k; ++q) {
-                    int64_t a = toff[T] + q * ch, b = std::min(toff[T + 1], a + ch);
-                    items.push_back(Item{(int32_t)T, slots + (int32_t)q, a, b});
-                }
-                slots += (int32_t)k;
-            }
-        }
-        std::stable_sort(items.begin(), items.end(),
-                         [](const Item& x, const Item& y) { return (x.e1 - x.e0) > (y.e1 - y.e0); });
-        g->n_items = (int32_t)items.size();
-        g->n_slots = slots;
-        GEOM_TRY(dmalloc(g, &g->items, items.size()));
-        GEOM_TRY(dmalloc(g, &g->tile_slot0, g->n_tiles));
-        GEOM_TRY(dmalloc(g, &g->tile_nslot, g->n_tiles));
-        GEOM_TRY(dmalloc(g, &g->jpart, (size_t)g->E * APPLY_WARPS));
-        GEOM_TRY(dmalloc(g, &g->gpart, (size_t)slots * TILE_VOX));
-        GEOM_TRY(dmalloc(g, &g->counter, 4));
-        if (!items.empty())
-            GEOM_CUDA(cudaMemcpy(g->items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
-        GEOM_CUDA(cudaMemcpy(g->tile_slot0, slot0.data(), sizeof(int32_t) * g->n_tiles, cudaMemcpyHostToDevice));
-        GEOM_CUDA(cudaMemcpy(g->tile_nslot, nslot.data(), sizeof(int32_t) * g->n_tiles, cudaMemcpyHostToDevice));
-    }
+    GEOM_TRY(dmalloc(g, &g->jpart, (size_t)g->E * APPLY_WARPS));
+    GEOM_TRY(dmalloc(g, &g->counter, 4));
+    GEOM_TRY(build_items(g, toff, DEFAULT_ITEMS_PER_CTA));
     GEOM_CUDA(cudaDeviceSynchronize());
     GEOM_TRY(count_support(g, &g->support, &g->evaluated));
     GEOM_CUDA(cudaDeviceSynchronize());
