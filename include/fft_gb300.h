@@ -124,7 +124,10 @@ fft_status fft_trig_build(const fft_spectrum* spec, double dt_max, int32_t n_ter
  *   band_of_row  host, nullable (all rows use table 0), else n_rows table indices.
  *   grid         voxel grid (host struct).
  *   c0           background sound speed (m/s) > 0.
- *   tables       host array of n_tables handles (1..8).
+ *   tables       host array of n_tables handles (1..8). The kernels hold every table in shared
+ *                memory: n_tables x n_samples x 8 bytes + 16 KB must fit in the device's per-CTA
+ *                shared memory (227 KB on sm_103a: up to 6 tables of 4096 samples, 8 of 2048),
+ *                else FFT_ERR_ARG.
  *   dt_mode      FFT_DT_STABLE / FFT_DT_NAIVE / FFT_DT_FP64.
  * Builds per-row records and the culled (tile, row) lists on the device: a (16x16x8 voxel
  * tile, row) entry is kept unless a lower bound of the detour over the tile (tangent plane
