@@ -48,21 +48,43 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 
 // Conservative test: may the row's support {R < 1} (band units) reach a box of voxel
 // centres with centre c and half extents hx, hy, hz? R(x) = |x - xs| + |x - xr| - 2 hl is
-// convex, so R(x) >= R(c) + grad R(c) . (x - c) >= R(c) - sum_k |dR/dx_k(c)| half_k over the
-// box. d = c - o is the centre relative to the pair midpoint, e the unit pair axis.
-__device__ __forceinline__ bool box_may_touch(float dx, float dy, float dz, float ex, float ey,
-                                              float ez, float hl, float hx, float hy, float hz) {
-    float sx = dx + hl * ex, sy = dy + hl * ey, sz = dz + hl * ez;   // c - xs
-    float rx = dx - hl * ex, ry = dy - hl * ey, rz = dz - hl * ez;   // c - xr
+// convex, so every tangent plane lies below it: R(x) >= R(x1) + grad R(x1) . (x - x1), whose
+// minimum over the box is R(x1) + grad R(x1) . (c - x1) - sum_k |dR/dx_k(x1)| half_k. The box
+// is culled when that minimum reaches 1 for the plane at the centre, or for a second plane
+// at the corner where the centre's plane is lowest (which removes most of the boxes the first
+// plane keeps without any in-support voxel centre). d = c - o is the centre relative to the
+// pair midpoint, e the unit pair axis.
+__device__ __forceinline__ float tangent_box_min(float x1x, float x1y, float x1z, float cx, float cy, float cz,
+                                                 float ex, float ey, float ez, float hl, float hx, float hy,
+                                                 float hz, bool& ok) {
+    const float sx = x1x + hl * ex, sy = x1y + hl * ey, sz = x1z + hl * ez;   // x1 - xs
+    const float rx = x1x - hl * ex, ry = x1y - hl * ey, rz = x1z - hl * ez;   // x1 - xr
     const float ss = sx * sx + sy * sy + sz * sz, rr = rx * rx + ry * ry + rz * rz;
-    if (!(ss > 1e-12f) || !(rr > 1e-12f)) return true;
+    ok = (ss > 1e-12f) && (rr > 1e-12f);
     // approximate reciprocal square roots (relative error ~1e-7): the bound's error is a few
     // 1e-5 band units at most, far inside CULL_MARGIN
+    const float is = rsqrt_approx(fmaxf(ss, 1e-12f)), ir = rsqrt_approx(fmaxf(rr, 1e-12f));
+    const float gx = sx * is + rx * ir, gy = sy * is + ry * ir, gz = sz * is + rz * ir;
+    const float lin = gx * (cx - x1x) + gy * (cy - x1y) + gz * (cz - x1z);
+    return (ss * is + rr * ir - 2.0f * hl) + lin - (fabsf(gx) * hx + fabsf(gy) * hy + fabsf(gz) * hz);
+}
+
+__device__ __forceinline__ bool box_may_touch(float dx, float dy, float dz, float ex, float ey,
+                                              float ez, float hl, float hx, float hy, float hz) {
+    const float sx = dx + hl * ex, sy = dy + hl * ey, sz = dz + hl * ez;   // c - xs
+    const float rx = dx - hl * ex, ry = dy - hl * ey, rz = dz - hl * ez;   // c - xr
+    const float ss = sx * sx + sy * sy + sz * sz, rr = rx * rx + ry * ry + rz * rz;
+    if (!(ss > 1e-12f) || !(rr > 1e-12f)) return true;
     const float is = rsqrt_approx(ss), ir = rsqrt_approx(rr);
     const float Rs = ss * is, Rr = rr * ir;
-    float gx = sx * is + rx * ir, gy = sy * is + ry * ir, gz = sz * is + rz * ir;
-    float lb = (Rs + Rr - 2.0f * hl) - (fabsf(gx) * hx + fabsf(gy) * hy + fabsf(gz) * hz);
-    return !(lb >= 1.0f + CULL_MARGIN);   // NaN keeps the entry
+    const float gx = sx * is + rx * ir, gy = sy * is + ry * ir, gz = sz * is + rz * ir;
+    const float lb = (Rs + Rr - 2.0f * hl) - (fabsf(gx) * hx + fabsf(gy) * hy + fabsf(gz) * hz);
+    if (!(lb < 1.0f + CULL_MARGIN)) return false;   // NaN keeps the entry
+    // second plane at the corner x1 = c - sign(grad R(c)) * half
+    const float x1x = dx - copysignf(hx, gx), x1y = dy - copysignf(hy, gy), x1z = dz - copysignf(hz, gz);
+    bool ok;
+    const float lb1 = tangent_box_min(x1x, x1y, x1z, dx, dy, dz, ex, ey, ez, hl, hx, hy, hz, ok);
+    return !(ok && lb1 >= 1.0f + CULL_MARGIN);
 }
 
 // Normalised detour v = R / U in [0, 1] (saturated) and the two inverse distances, from
