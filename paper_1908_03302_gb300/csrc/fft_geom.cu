@@ -30,6 +30,7 @@ struct CullParams {
     const BandConst* bc;
     int64_t M;
     int tiles_x, tiles_y;
+    int nx, ny, nz;
 };
 
 __device__ __forceinline__ bool tile_keeps_row(const CullParams& C, int T, int64_t p) {
@@ -40,8 +41,23 @@ __device__ __forceinline__ bool tile_keeps_row(const CullParams& C, int T, int64
     const float cx = fmaf((float)(TILE_X * tx) + 0.5f * (TILE_X - 1), hb, bc.org[0]) - r.a.x;
     const float cy = fmaf((float)(TILE_Y * ty) + 0.5f * (TILE_Y - 1), hb, bc.org[1]) - r.a.y;
     const float cz = fmaf((float)(TILE_Z * tz) + 0.5f * (TILE_Z - 1), hb, bc.org[2]) - r.a.z;
-    return box_may_touch(cx, cy, cz, r.b.x, r.b.y, r.b.z, r.a.w, 0.5f * (TILE_X - 1) * hb,
-                         0.5f * (TILE_Y - 1) * hb, 0.5f * (TILE_Z - 1) * hb);
+    if (!box_may_touch(cx, cy, cz, r.b.x, r.b.y, r.b.z, r.a.w, 0.5f * (TILE_X - 1) * hb,
+                       0.5f * (TILE_Y - 1) * hb, 0.5f * (TILE_Z - 1) * hb))
+        return false;
+    // keep the row only if one of the tile's 16 sub-bricks (8 x 4 x 4, the apply kernels'
+    // culling unit) inside the grid may reach the support: rows that reach none of them
+    // would be staged by every region for nothing
+    const float x0 = cx - 0.5f * (TILE_X - 1) * hb, y0 = cy - 0.5f * (TILE_Y - 1) * hb,
+                z0 = cz - 0.5f * (TILE_Z - 1) * hb;
+    for (int sb = 0; sb < 16; ++sb) {
+        const int sx = 8 * (sb & 1), sy = 4 * ((sb >> 1) & 3), sz = 4 * (sb >> 3);
+        if (TILE_X * tx + sx >= C.nx || TILE_Y * ty + sy >= C.ny || TILE_Z * tz + sz >= C.nz) continue;
+        if (box_may_touch(fmaf((float)sx + 3.5f, hb, x0), fmaf((float)sy + 1.5f, hb, y0),
+                          fmaf((float)sz + 1.5f, hb, z0), r.b.x, r.b.y, r.b.z, r.a.w, 3.5f * hb, 1.5f * hb,
+                          1.5f * hb))
+            return true;
+    }
+    return false;
 }
 
 __global__ void tile_count_kernel(const CullParams C, int64_t* __restrict__ cnt) {
@@ -488,6 +504,9 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     C.bc = g->d_band;
     C.M = n_rows;
     C.tiles_x = g->tiles[0];
+    C.nx = grid->nx;
+    C.ny = grid->ny;
+    C.nz = grid->nz;
     C.tiles_y = g->tiles[1];
 
     std::vector<int64_t> tcnt(g->n_tiles), toff(g->n_tiles + 1, 0);
