@@ -172,8 +172,10 @@ typedef struct {
  * fft_geom_autotune - pick the work decomposition of J and J^T for this geometry by timing
  * them on the device: a tile's candidate rows are cut into work items sized for 4, 8, 16, 32,
  * 64 or 128 items per persistent CTA (at least 64 rows each), with the most CTAs per SM that
- * fit or one fewer; each of the twelve candidates runs J^T and J once untimed and once timed
- * (CUDA events on `stream`),
+ * fit or one fewer. The sizes are swept at the occupancy limit (stopping after two in a row
+ * more than 2 % slower than the best), then the best size and its two neighbours with one CTA
+ * per SM fewer: 2 to 9 candidates. Each runs J^T and J once timed (CUDA events on `stream`),
+ * after one untimed pass unless the previous candidate's pair took over 20 ms,
  * and the fastest is kept (results do not depend on it beyond rounding of the split J^T
  * sums). Synchronous; allocates test vectors for the duration of the call; invalidates a
  * captured CG loop (the next fft_cg_solve captures again). info may be NULL.

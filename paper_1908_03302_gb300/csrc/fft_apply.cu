@@ -14,8 +14,10 @@
 //     detour (cancellation-free form), Phi from the band table in shared memory (one 64-bit
 //     load, linear interpolation), geometric factor 1 / (R_xs R_xr).
 //   * J^T accumulates per voxel in registers over the item's rows (gather, no atomics).
-//     J reduces per row over the warp (shuffles) and writes one partial per (entry, warp);
-//     a second kernel sums each row's partials in a fixed order. Both are deterministic.
+//     J folds each row's lane partials to 8 with two shuffles, parks them in the row's
+//     consumed staging record, and the row's own lane sums them after the chunk: one partial
+//     per (entry, warp); a second kernel sums each row's partials in a fixed order. Both are
+//     deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -442,8 +444,13 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHAR
                     }
                 }
                 if (MODE == MODE_J) {
-                    part = warp_sum(part);
-                    if (lane == bit) mypart = part * W;
+                    // Fold the row's 32 lane partials to 8 (lanes 0-7 then hold distinct sums)
+                    // and park them in the row's own staged record, which every lane has read
+                    // by now; the row's lane adds the 8 in a fixed order after the chunk.
+                    part += __shfl_xor_sync(0xffffffffu, part, 16);
+                    part += __shfl_xor_sync(0xffffffffu, part, 8);
+                    __syncwarp();
+                    if (lane < 8) reinterpret_cast<float*>(stg + bit * SR)[lane] = part;
                 }
                 if (MODE == MODE_J4) {
 #pragma unroll
@@ -454,7 +461,18 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHAR
                 }
                 if (MODE == MODE_FROB) dacc += (double)part * (double)W * (double)W;
             }
-            if (MODE == MODE_J && have) P.vout[e * 8 + region] = mypart;
+            if (MODE == MODE_J) {
+                __syncwarp();
+                if (have) {
+                    if (((m0 | m1) >> lane) & 1u) {
+                        const float4 r0 = stg[lane * SR + 0];
+                        const float4 r1 = stg[lane * SR + 1];
+                        const float Wl = stg[lane * SR + 2].x;
+                        mypart = (r0.x + r0.y + r0.z + r0.w + r1.x + r1.y + r1.z + r1.w) * Wl;
+                    }
+                    P.vout[e * 8 + region] = mypart;
+                }
+            }
             if (MODE == MODE_J4 && have)
                 *reinterpret_cast<float4*>(P.vout + (e * 8 + region) * 4) =
                     make_float4(mypart4[0], mypart4[1], mypart4[2], mypart4[3]);

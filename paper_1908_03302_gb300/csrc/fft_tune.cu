@@ -52,37 +52,55 @@ extern "C" fft_status fft_geom_autotune(fft_geom g, void* stream, fft_tune_info_
         tune_fill_kernel<<<(unsigned)ceil_div(g->M, 256), 256, 0, st>>>(d, g->M, 1e-8f);
         e = cudaGetLastError();
     }
+    // Search: all item sizes at the occupancy limit (stopping once two sizes in a row are
+    // slower than the best by more than 2 %), then one CTA per SM fewer around the best size.
+    // A candidate gets an untimed pass first unless the last application took over 20 ms
+    // (then first-launch effects are lost in the measurement and the pass would double the
+    // cost of tuning a large acquisition).
     const int cand_items[] = {4, 8, 16, 32, 64, 128};
-    double best = 1e300, best_j = 0.0, best_jt = 0.0;
-    int best_items = g->items_per_cta, best_ctas = g->apply_ctas / std::max(sms, 1), tried = 0;
-    for (int ci = 0; ci < 2 && e == cudaSuccess && rc == FFT_OK; ++ci) {
-        const int ctas = occ - ci;
-        if (ctas < 1) break;
-        for (int ii = 0; ii < 6 && e == cudaSuccess && rc == FFT_OK; ++ii) {
-            g->apply_ctas = ctas * sms;
-            if ((rc = build_items(g, toff, cand_items[ii])) != FFT_OK) break;
-            // one untimed pass, then time J^T and J once (the applications are long enough
-            // that one event pair resolves them)
-            if ((rc = launch_JT(g, d, out_v, st)) != FFT_OK) break;
-            if ((rc = launch_J(g, m, out_m, st)) != FFT_OK) break;
-            e = cudaEventRecord(e0, st);
-            if (e == cudaSuccess && (rc = launch_JT(g, d, out_v, st)) != FFT_OK) break;
-            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess && (rc = launch_J(g, m, out_m, st)) != FFT_OK) break;
-            if (e == cudaSuccess) e = cudaEventRecord(e2, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e2);
-            float ms_jt = 0.0f, ms_j = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_jt, e0, e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_j, e1, e2);
-            if (e != cudaSuccess) break;
-            ++tried;
-            if (ms_j + ms_jt < best) {
-                best = ms_j + ms_jt;
-                best_j = ms_j;
-                best_jt = ms_jt;
-                best_items = cand_items[ii];
-                best_ctas = ctas;
-            }
+    const int n_cand = 6;
+    double best = 1e300, best_j = 0.0, best_jt = 0.0, last = 0.0;
+    int best_items = g->items_per_cta, best_ctas = g->apply_ctas / std::max(sms, 1), tried = 0, best_ii = 0;
+    auto try_one = [&](int ctas, int ii) -> bool {
+        g->apply_ctas = ctas * sms;
+        if ((rc = build_items(g, toff, cand_items[ii])) != FFT_OK) return false;
+        if (tried == 0 || last < 20.0) {
+            if ((rc = launch_JT(g, d, out_v, st)) != FFT_OK) return false;
+            if ((rc = launch_J(g, m, out_m, st)) != FFT_OK) return false;
+        }
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess && (rc = launch_JT(g, d, out_v, st)) != FFT_OK) return false;
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess && (rc = launch_J(g, m, out_m, st)) != FFT_OK) return false;
+        if (e == cudaSuccess) e = cudaEventRecord(e2, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e2);
+        float ms_jt = 0.0f, ms_j = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_jt, e0, e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_j, e1, e2);
+        if (e != cudaSuccess) return false;
+        ++tried;
+        last = (double)ms_j + ms_jt;
+        if (last < best) {
+            best = last;
+            best_j = ms_j;
+            best_jt = ms_jt;
+            best_items = cand_items[ii];
+            best_ii = ii;
+            best_ctas = ctas;
+        }
+        return true;
+    };
+    if (e == cudaSuccess) {
+        int worse = 0;
+        for (int ii = 0; ii < n_cand; ++ii) {
+            if (!try_one(occ, ii)) break;
+            worse = (last > 1.02 * best) ? worse + 1 : 0;
+            if (worse == 2) break;
+        }
+        if (e == cudaSuccess && rc == FFT_OK && occ > 1) {
+            const int centre = best_ii;
+            for (int ii = std::max(0, centre - 1); ii <= std::min(n_cand - 1, centre + 1); ++ii)
+                if (!try_one(occ - 1, ii)) break;
         }
     }
     if (e == cudaSuccess && rc == FFT_OK) {

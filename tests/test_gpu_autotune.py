@@ -1,5 +1,5 @@
-"""The work-decomposition autotuner (fft_geom_autotune): it times twelve candidates, keeps one of
-them, and the operator it leaves behind still matches the FP64 oracle (J bit for bit as
+"""The work-decomposition autotuner (fft_geom_autotune): it times up to nine of twelve
+candidates, keeps one of them, and the operator it leaves behind still matches the FP64 oracle (J bit for bit as
 before: its per-row sums do not depend on the items; J^T within rounding), including a CG
 solve whose captured loop the tuner invalidates."""
 import numpy as np
@@ -32,7 +32,7 @@ def test_autotune_keeps_the_operator(fg, name):
     if name == "ring32":   # a captured CG loop before tuning
         m_cg0 = geo.cg_solve(J0, w.lambda_rel, 5)
     t = geo.autotune()
-    assert t["candidates"] in (6, 12)
+    assert 2 <= t["candidates"] <= 9
     assert t["items_per_cta"] in (4, 8, 16, 32, 64, 128) and t["ctas_per_sm"] >= 1
     assert t["ms_J"] > 0 and t["ms_JT"] > 0
     assert torch.equal(geo.J(m), J0)
