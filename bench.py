@@ -442,6 +442,22 @@ def run_lowrank(args, ws, rank, local):
 
 # --------------------------------------------------------------------------- GPU arm
 
+def nvtx_push(name):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:   # NVTX is only a marker for profilers
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,6 +537,7 @@ def main():
         r0 = torch.randn(geo.M, device=dev, dtype=torch.float32) * 1e-8
         g0 = torch.empty(geo.V, device=dev, dtype=torch.float32)
         for i in range(args.warmup + args.steps):
+            nvtx_push("apply")   # lets a profiler skip the autotuner's launches of the same kernels
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             geo.JT(r0, out=g0)
@@ -530,6 +547,7 @@ def main():
             geo.J(m_true, out=d)
             e.record(stream)
             torch.cuda.synchronize()
+            nvtx_pop()
             if rank == 0:
                 print(json.dumps({"apply": i, "ms_JT": a.elapsed_time(b), "ms_J": c.elapsed_time(e),
                                   "support": support, "evaluated": int(info.evaluated_evals),

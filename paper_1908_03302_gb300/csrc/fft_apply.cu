@@ -583,46 +583,61 @@ __global__ void __launch_bounds__(256) j_reduce4_kernel(const int64_t* __restric
     }
 }
 
-// The four-column form of jt_reduce_kernel: slot q of column r at gpart4[((s0 + q) * 4 + r)
-// * TILE_VOX + loc], g[r * V + v].
-__global__ void jt_reduce4_kernel(const int32_t* __restrict__ slot0, const int32_t* __restrict__ nslot,
-                                  const float* __restrict__ gpart4, int nx, int ny, int nz, int tiles_x,
-                                  int tiles_y, float* __restrict__ g) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t V = (int64_t)nx * ny * nz;
-    if (v >= V) return;
-    int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
-    int T = (k / TILE_Z * tiles_y + j / TILE_Y) * tiles_x + i / TILE_X;
-    int s0 = slot0[T];
+// g for voxels of tiles with several items (the slots summed in item order) or with none (0);
+// tiles with one item were written by the apply kernel. One thread takes 4 consecutive x
+// voxels of a tile (512 threads per tile); the slots are read 4 at a time so that several
+// loads are in flight, and added one by one from 0 in slot order (deterministic).
+// NCOL = 4: the four-column form, slot q of column r at gpart[((s0 + q) * 4 + r) * TILE_VOX],
+// g[r * V + v].
+template <int NCOL>
+__global__ void __launch_bounds__(256) jt_reduce_kernel(const int32_t* __restrict__ slot0,
+                                                        const int32_t* __restrict__ nslot,
+                                                        const float* __restrict__ gpart, int64_t n_tiles, int nx,
+                                                        int ny, int nz, int tiles_x, int tiles_y,
+                                                        float* __restrict__ g) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_tiles * (TILE_VOX / 4)) return;
+    const int T = (int)(idx / (TILE_VOX / 4));
+    const int s0 = slot0[T];
     if (s0 == -1) return;
-    int loc = ((k % TILE_Z) * TILE_Y + (j % TILE_Y)) * TILE_X + (i % TILE_X);
-    for (int r = 0; r < 4; ++r) {
-        float s = 0.0f;
-        if (s0 != -2)
-            for (int q = 0; q < nslot[T]; ++q) s += gpart4[((int64_t)(s0 + q) * 4 + r) * TILE_VOX + loc];
-        g[(int64_t)r * V + v] = s;
+    const int loc = 4 * (int)(idx % (TILE_VOX / 4));
+    const int ix = TILE_X * (T % tiles_x) + loc % TILE_X;
+    const int iy = TILE_Y * ((T / tiles_x) % tiles_y) + (loc / TILE_X) % TILE_Y;
+    const int iz = TILE_Z * (T / (tiles_x * tiles_y)) + loc / (TILE_X * TILE_Y);
+    if (iy >= ny || iz >= nz || ix >= nx) return;
+    const int64_t V = (int64_t)nx * ny * nz;
+    const int64_t v = ((int64_t)iz * ny + iy) * nx + ix;
+    const int ns = (s0 == -2) ? 0 : nslot[T];
+#pragma unroll
+    for (int r = 0; r < NCOL; ++r) {
+        float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const float* base = ns > 0 ? gpart + ((int64_t)s0 * NCOL + r) * TILE_VOX + loc : nullptr;
+        int q = 0;
+        for (; q + 4 <= ns; q += 4) {
+            float4 w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w[k] = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)(q + k) * NCOL * TILE_VOX));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                acc.x += w[k].x;
+                acc.y += w[k].y;
+                acc.z += w[k].z;
+                acc.w += w[k].w;
+            }
+        }
+        for (; q < ns; ++q) {
+            const float4 w = __ldcs(reinterpret_cast<const float4*>(base + (int64_t)q * NCOL * TILE_VOX));
+            acc.x += w.x;
+            acc.y += w.y;
+            acc.z += w.z;
+            acc.w += w.w;
+        }
+        float* out = g + (int64_t)r * V + v;
+        out[0] = acc.x;
+        if (ix + 1 < nx) out[1] = acc.y;
+        if (ix + 2 < nx) out[2] = acc.z;
+        if (ix + 3 < nx) out[3] = acc.w;
     }
-}
-
-// g for voxels of tiles with several items (sum of slots in item order) or with none (0).
-__global__ void jt_reduce_kernel(const int32_t* __restrict__ slot0, const int32_t* __restrict__ nslot,
-                                 const float* __restrict__ gpart, int nx, int ny, int nz, int tiles_x,
-                                 int tiles_y, float* __restrict__ g) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t V = (int64_t)nx * ny * nz;
-    if (v >= V) return;
-    int i = (int)(v % nx), j = (int)((v / nx) % ny), k = (int)(v / ((int64_t)nx * ny));
-    int T = (k / TILE_Z * tiles_y + j / TILE_Y) * tiles_x + i / TILE_X;
-    int s0 = slot0[T];
-    if (s0 == -1) return;
-    if (s0 == -2) {
-        g[v] = 0.0f;
-        return;
-    }
-    int loc = ((k % TILE_Z) * TILE_Y + (j % TILE_Y)) * TILE_X + (i % TILE_X);
-    float s = 0.0f;
-    for (int q = 0; q < nslot[T]; ++q) s += gpart[(int64_t)(s0 + q) * TILE_VOX + loc];
-    g[v] = s;
 }
 
 static ApplyParams make_params(fft_geom g) {
@@ -822,6 +837,17 @@ fft_status launch_J_batch(fft_geom g, const float* m, int n, float* d, cudaStrea
     return FFT_OK;
 }
 
+template <int NCOL>
+static fft_status launch_jt_reduce(fft_geom g, const float* gpart, float* gout, cudaStream_t st) {
+    const int64_t threads = g->n_tiles * (TILE_VOX / 4);
+    if (threads == 0) return FFT_OK;
+    jt_reduce_kernel<NCOL><<<(unsigned)ceil_div(threads, 256), 256, 0, st>>>(
+        g->tile_slot0, g->tile_nslot, gpart, g->n_tiles, g->grid.nx, g->grid.ny, g->grid.nz, g->tiles[0],
+        g->tiles[1], gout);
+    FFT_CUDA(cudaGetLastError());
+    return FFT_OK;
+}
+
 // g[:, c] = J^T d[:, c] for n columns (groups of four as above).
 fft_status launch_JT_batch(fft_geom g, const float* din, int n, float* gout, cudaStream_t st) {
     int c = 0;
@@ -834,11 +860,7 @@ fft_status launch_JT_batch(fft_geom g, const float* din, int n, float* gout, cud
             P.vout = gout + (int64_t)c * g->V;
             P.gpart = g->gpart4;
             if ((rc = launch_batch<MODE_JT4>(g, P, st)) != FFT_OK) return rc;
-            jt_reduce4_kernel<<<(unsigned)ceil_div(g->V, 256), 256, 0, st>>>(g->tile_slot0, g->tile_nslot, g->gpart4,
-                                                                          g->grid.nx, g->grid.ny, g->grid.nz,
-                                                                          g->tiles[0], g->tiles[1],
-                                                                          gout + (int64_t)c * g->V);
-            FFT_CUDA(cudaGetLastError());
+            if ((rc = launch_jt_reduce<4>(g, g->gpart4, gout + (int64_t)c * g->V, st)) != FFT_OK) return rc;
         }
     }
     for (; c < n; ++c) {
@@ -868,10 +890,7 @@ fft_status launch_JT(fft_geom g, const float* din, float* gout, cudaStream_t st)
     P.vout = gout;
     fft_status rc = launch_mode<MODE_JT>(g, P, st);
     if (rc != FFT_OK) return rc;
-    int64_t blocks = ceil_div(g->V, 256);
-    jt_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->tile_slot0, g->tile_nslot, g->gpart, g->grid.nx,
-                                                       g->grid.ny, g->grid.nz, g->tiles[0], g->tiles[1], gout);
-    FFT_CUDA(cudaGetLastError());
+    return launch_jt_reduce<1>(g, g->gpart, gout, st);
     return FFT_OK;
 }
 
@@ -882,10 +901,7 @@ fft_status launch_cov(fft_geom g, const float* w, float* cov, cudaStream_t st) {
     P.vout = cov;
     fft_status rc = launch_mode<MODE_COV>(g, P, st);
     if (rc != FFT_OK) return rc;
-    int64_t blocks = ceil_div(g->V, 256);
-    jt_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->tile_slot0, g->tile_nslot, g->gpart, g->grid.nx,
-                                                       g->grid.ny, g->grid.nz, g->tiles[0], g->tiles[1], cov);
-    FFT_CUDA(cudaGetLastError());
+    return launch_jt_reduce<1>(g, g->gpart, cov, st);
     return FFT_OK;
 }
 
