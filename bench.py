@@ -43,10 +43,10 @@ UNIT = "eval/s"
 # 2 (index, fraction), 2 (lerp), 1 (rsqrt product), 1 (times Phi), 1 (accumulate).
 OPS_PER_EVAL = 24
 FP32_LANES_PER_SM_CLK = 128
-# DRAM bytes (read + write) of one J^T apply-kernel launch on this workload, from the ncu
-# capture summarised in profiles/apply_kernel_ring256.md; None until captured for the
-# current kernel.
-APPLY_TRAFFIC_BYTES = 125214720   # 101971712 read + 23243008 written (ncu, one J^T launch on ring256)
+# DRAM bytes (read + write) of one J^T on ring256 (the apply kernel and its slot reduction,
+# as timed), from the ncu capture summarised in profiles/apply_kernel_ring256.md; None until
+# captured for the current kernels.
+APPLY_TRAFFIC_BYTES = 352048896   # apply 87316224 + 109712896, jt_reduce 151964672 + 3055104
 
 
 def peaks():
@@ -465,7 +465,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="ring256",
-                    choices=["ring32", "ring256", "slices3d", "psf3d", "spacing", "lowrank"])
+                    choices=["ring32", "ring256", "ring256_3band", "slices3d", "psf3d", "spacing", "lowrank"])
     ap.add_argument("--lowrank-k", type=int, default=64)
     ap.add_argument("--psf-spikes", type=int, default=128)
     ap.add_argument("--psf-fp32-spikes", type=int, default=8)
@@ -694,7 +694,9 @@ def main():
         "setup_ms": {"table": 1e3 * (t1 - t0), "geometry_and_cull": 1e3 * (t2 - t1), "autotune": 1e3 * (t3 - t2)},
         "autotune": tuning,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
-                     "frac": achieved / peak_evals, "traffic": APPLY_TRAFFIC_BYTES,
+                     "frac": achieved / peak_evals,
+                     "traffic": APPLY_TRAFFIC_BYTES if (w.name == "ring256" and args.dt_mode == 0 and n_terms == 0)
+                     else None,
                      "kernel": "apply_kernel (J^T) + jt_reduce",
                      "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM_CLK} FP32 lanes x {sm_max:.0f} MHz "
                                    f"({pk_kind}) / {ops} ops per eval"},

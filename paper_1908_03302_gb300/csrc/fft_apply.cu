@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -116,8 +117,101 @@ constexpr int apply_min_blocks() {
                                                           : ((DT == FFT_DT_STABLE && PHI == PHI_TABLE) ? 4 : 3);
 }
 
+// The FP64 re-decision of the sharp-band kernels, out of line (called only for an entry where
+// some lane's FP32 detour lies within CUT_BAND of the cut), so that its FP64 temporaries do not
+// weigh on the register allocation of the main loop. For each of the lane's 8 voxels (k = 4 s
+// + t) it recomputes the FP32 detour by the operations of the main pass, and for the voxels
+// near the cut re-decides dt < dt_max in FP64. It returns in d[k] what the main pass's term
+// has to change by: val2 - val1 (J, J^T, four-column modes), |val2| - |val1| (coverage),
+// val2^2 - val1^2 (Frobenius), +1 / -1 (support count), 0 where nothing changes.
+// UNROLL: 8 when inlined (d stays in registers), 1 out of line.
+template <int MODE, int DT, bool GUARD, int PHI, int UNROLL>
+__device__ __forceinline__ void sharp_fix_body(const ApplyParams& P, float4 A, float4 B, float4 C, float Xl,
+                                               float Yl, float Zl, bool planar, bool inner0, bool inner1, float cutb,
+                                               uint32_t tb, float nm1, int nq, int ix0, int iy0, int iz0, float* d) {
+    const float hx = B.x, hy = B.y, hz = B.z;
+    const float hl = 0.5f * (A.x - A.y);
+    const int b = __float_as_int(C.w) & 0xff;
+    const double U = P.bc[b].U;
+#pragma unroll UNROLL
+    for (int k = 0; k < 8; ++k) {
+        const int s = k >> 2, t = k & 3;
+        d[k] = 0.0f;
+        const float offs = fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
+        float pss = A.x + offs, prs = A.y + offs;
+        float c1s = fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
+        const float c2s = fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
+        float c3s = fmaf(Xl, hy, fmaf(-Yl, hx, B.w));
+        if (s == 1) {
+            pss = fmaf(4.0f, hy, pss);
+            prs = fmaf(4.0f, hy, prs);
+            c1s = fmaf(4.0f, hz, c1s);
+            c3s = fmaf(-4.0f, hx, c3s);
+        }
+        const float ft = (float)t;
+        const float c1sq = c1s * c1s;
+        const float pst = fmaf(ft, hx, pss);
+        const float prt = fmaf(ft, hx, prs);
+        const float c3t = fmaf(ft, hy, c3s);
+        float q2;
+        if (planar) {
+            q2 = fmaf(c3t, c3t, fmaf(c2s, c2s, c1sq));
+        } else {
+            const float c2t = fmaf(-ft, hz, c2s);
+            q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
+        }
+        const bool inner = (DT == FFT_DT_STABLE) && (s ? inner1 : inner0);
+        float is, ir;
+        const float vr = inner ? detour_v<DT, GUARD, true, true>(pst, prt, q2, hl, is, ir)
+                               : detour_v<DT, GUARD, false, true>(pst, prt, q2, hl, is, ir);
+        if (!(fabsf(vr - 1.0f) < cutb)) continue;
+        const float v = __saturatef(vr);
+        const bool in = in_support64(P.rec64[__float_as_int(C.z)], P.org[0], P.org[1], P.org[2], P.h, ix0 + t,
+                                     iy0 + 4 * s, iz0, U);
+        const float v2 = settle_cut(v, in);
+        if (v2 == v) continue;
+        if (MODE == MODE_COUNT) {
+            d[k] = (v2 < 1.0f) ? 1.0f : -1.0f;
+            continue;
+        }
+        const float w = is * ir;
+        const float val1 = phi_eval<PHI>(v, tb, nm1, nq) * w;
+        const float val2 = phi_eval<PHI>(v2, tb, nm1, nq) * w;
+        if (MODE == MODE_COV) d[k] = fabsf(val2) - fabsf(val1);
+        else if (MODE == MODE_FROB) d[k] = val2 * val2 - val1 * val1;
+        else d[k] = val2 - val1;
+    }
+}
+
+// Out of line for the modes where that measured faster (J, the set-up counts, the four-column
+// modes); J^T and the coverage keep it inline, where saving their eight live accumulators
+// around a call costs more than the registers it frees.
+template <int MODE>
+constexpr bool sharp_fix_outlined() {
+    return MODE != MODE_JT && MODE != MODE_COV;
+}
+
+template <int MODE, int DT, bool GUARD, int PHI>
+__device__ __noinline__ void sharp_fix(const ApplyParams& P, float4 A, float4 B, float4 C, float Xl, float Yl,
+                                       float Zl, bool planar, bool inner0, bool inner1, float cutb, uint32_t tb,
+                                       float nm1, int nq, int ix0, int iy0, int iz0, float* d) {
+    sharp_fix_body<MODE, DT, GUARD, PHI, 1>(P, A, B, C, Xl, Yl, Zl, planar, inner0, inner1, cutb, tb, nm1, nq, ix0,
+                                            iy0, iz0, d);
+}
+
+// The sharp-band stable-detour table variants (single column) are built for CTAs of up to 24
+// warps at one per SM (at most 85 registers): as 8-warp CTAs three fit per SM on register
+// count, and where large band tables leave room for fewer, one CTA of 16 or 24 warps shares
+// one copy of the tables.
+template <int MODE, int DT, bool SHARP, int PHI>
+constexpr bool apply_sharp_wide() {
+    return SHARP && DT == FFT_DT_STABLE && PHI == PHI_TABLE && MODE != MODE_JT4 && MODE != MODE_J4;
+}
+constexpr int SHARP_MAX_WARPS = 24;
+
 template <int MODE, int DT, bool GUARD, bool SHARP, int PHI>
-__global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHARP, PHI>())
+__global__ void __launch_bounds__(apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 32 * SHARP_MAX_WARPS : APPLY_THREADS,
+                                  apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 1 : apply_min_blocks<MODE, DT, SHARP, PHI>())
     apply_kernel(const __grid_constant__ ApplyParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* s_tab = reinterpret_cast<float2*>(smem);
@@ -125,7 +219,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHAR
     float4* s_stage = reinterpret_cast<float4*>(smem + (((size_t)tab_len * sizeof(float2) + 15) & ~(size_t)15));
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < tab_len; i += APPLY_THREADS) s_tab[i] = P.tab[i];
+    for (int i = tid; i < tab_len; i += blockDim.x) s_tab[i] = P.tab[i];
     __syncthreads();   // the only CTA-wide barrier: from here on every warp runs on its own
 
     const uint32_t tab_addr = smem_addr(s_tab);
@@ -135,7 +229,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHAR
     constexpr bool BATCH = (MODE == MODE_JT4 || MODE == MODE_J4);
     constexpr int SR = BATCH ? 4 : 3;   // staged float4 per row
     float4* stg = s_stage + warp * STG_PER_WARP;
-    const int n_units = P.n_items * APPLY_WARPS;
+    const int n_units = P.n_items * 8;   // 8 regions per item
 
     for (;;) {
         // A unit is one 8 x 8 x 4 region of one item (unit = item * 8 + region).
@@ -261,7 +355,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHAR
                 // voxels whose FP32 detour falls within CUT_BAND of a sharp band's cut-off
                 const float cutb = (SHARP && ((__float_as_int(C.w) >> 8) & 1)) ? CUT_BAND : -1.0f;
                 const bool planar = (DT != FFT_DT_FP64) && ((__float_as_int(C.w) >> 9) & 1);
-                uint32_t fix = 0;
+                bool near = false;   // a voxel of this lane has its FP32 detour within CUT_BAND of the cut
                 // lane base (sub-brick 0, t = 0) in the pair frame: small offsets added to the
                 // tile origin's FP64-derived values
                 float part = 0.0f;
@@ -314,7 +408,7 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHAR
             }                                                                                      \
             if (SHARP) {                                                                           \
                 v = detour_v<DT, GUARD, INNER_V, true>(pst, prt, q2, hl, is, ir);                  \
-                if (fabsf(v - 1.0f) < cutb) fix |= 1u << (4 * s + t);                              \
+                near |= (fabsf(v - 1.0f) < cutb);                                                  \
                 v = __saturatef(v);                                                                \
             } else {                                                                               \
                 v = detour_v<DT, GUARD, INNER_V>(pst, prt, q2, hl, is, ir);                        \
@@ -378,68 +472,39 @@ __global__ void __launch_bounds__(APPLY_THREADS, apply_min_blocks<MODE, DT, SHAR
                 else
                     entry_body(std::false_type{});
 #undef FFT_EVAL_SUB
-                if (SHARP && DT != FFT_DT_FP64 && __any_sync(0xffffffffu, fix != 0u)) {
-                    // Re-decide dt < dt_max in FP64 for the flagged voxels and correct what the
-                    // FP32 pass added (the FP32 value is recomputed by the same operations).
-                    const int b = __float_as_int(C.w) & 0xff;
-                    const double U = P.bc[b].U;
+                if (SHARP && DT != FFT_DT_FP64 && __any_sync(0xffffffffu, near)) {
+                    // FP64 re-decision of the voxels whose FP32 detour lies within CUT_BAND of
+                    // the cut; d[k] is the change of this entry's term for voxel k = 4 s + t
+                    float d[8];
+                    if (near) {
+                        if (sharp_fix_outlined<MODE>())
+                            sharp_fix<MODE, DT, GUARD, PHI>(P, A, B, C, Xl, Yl, Zl, planar, (i0 >> bit) & 1u,
+                                                            (i1 >> bit) & 1u, cutb, tb, nm1, nq, TX + oxi, TY + oyi,
+                                                            TZ + ozi, d);
+                        else
+                            sharp_fix_body<MODE, DT, GUARD, PHI, 8>(P, A, B, C, Xl, Yl, Zl, planar, (i0 >> bit) & 1u,
+                                                                    (i1 >> bit) & 1u, cutb, tb, nm1, nq, TX + oxi,
+                                                                    TY + oyi, TZ + ozi, d);
+                    }
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
 #pragma unroll
                         for (int t = 0; t < NX_LANE; ++t) {
-                            if (!((fix >> (4 * s + t)) & 1u)) continue;
-                            const float offs = fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
-                            float pss = A.x + offs, prs = A.y + offs;
-                            float c1s = fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
-                            const float c2s = fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
-                            float c3s = fmaf(Xl, hy, fmaf(-Yl, hx, B.w));
-                            if (s == 1) {
-                                pss = fmaf(4.0f, hy, pss);
-                                prs = fmaf(4.0f, hy, prs);
-                                c1s = fmaf(4.0f, hz, c1s);
-                                c3s = fmaf(-4.0f, hx, c3s);
-                            }
-                            const float ft = (float)t;
-                            const float c1sq = c1s * c1s;
-                            const float pst = fmaf(ft, hx, pss);
-                            const float prt = fmaf(ft, hx, prs);
-                            const float c3t = fmaf(ft, hy, c3s);
-                            float q2;
-                            if (planar) {
-                                q2 = fmaf(c3t, c3t, fmaf(c2s, c2s, c1sq));
-                            } else {
-                                const float c2t = fmaf(-ft, hz, c2s);
-                                q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
-                            }
-                            const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
-                            float is, ir;
-                            const float v = __saturatef(inner ? detour_v<DT, GUARD, true, true>(pst, prt, q2, hl, is, ir)
-                                                              : detour_v<DT, GUARD, false, true>(pst, prt, q2, hl, is, ir));
-                            const bool in = in_support64(P.rec64[__float_as_int(C.z)], P.org[0], P.org[1], P.org[2],
-                                                         P.h, TX + oxi + t, TY + oyi + 4 * s, TZ + ozi, U);
-                            const float v2 = settle_cut(v, in);
-                            if (v2 == v) continue;
-                            if (MODE == MODE_COUNT) {
-                                if ((vmask >> (4 * s + t)) & 1u) cnt += (v2 < 1.0f) ? 1ull : ~0ull;
-                                continue;
-                            }
-                            const float w = is * ir;
-                            const float val1 = phi_eval<PHI>(v, tb, nm1, nq) * w;
-                            const float val2 = phi_eval<PHI>(v2, tb, nm1, nq) * w;
-                            if (MODE == MODE_JT) acc[s][t] = fmaf(val2 - val1, W, acc[s][t]);
-                            if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val2) - fabsf(val1), W, acc[s][t]);
-                            if (MODE == MODE_J) part = fmaf(val2 - val1, mv[s][t], part);
+                            const float dk = near ? d[4 * s + t] : 0.0f;
+                            if (dk == 0.0f) continue;
+                            const bool valid = (vmask >> (4 * s + t)) & 1u;
+                            if (MODE == MODE_COUNT && valid) cnt += (dk > 0.0f) ? 1ull : ~0ull;
+                            if (MODE == MODE_JT || MODE == MODE_COV) acc[s][t] = fmaf(dk, W, acc[s][t]);
+                            if (MODE == MODE_J) part = fmaf(dk, mv[s][t], part);
                             if (MODE == MODE_JT4) {
 #pragma unroll
-                                for (int r = 0; r < 4; ++r) acc4[s][t][r] = fmaf(val2 - val1, Wr[r], acc4[s][t][r]);
+                                for (int r = 0; r < 4; ++r) acc4[s][t][r] = fmaf(dk, Wr[r], acc4[s][t][r]);
                             }
                             if (MODE == MODE_J4) {
 #pragma unroll
-                                for (int r = 0; r < 4; ++r) part4[r] = fmaf(val2 - val1, mv4[s][t][r], part4[r]);
+                                for (int r = 0; r < 4; ++r) part4[r] = fmaf(dk, mv4[s][t][r], part4[r]);
                             }
-                            if (MODE == MODE_FROB) {
-                                if ((vmask >> (4 * s + t)) & 1u) part += val2 * val2 - val1 * val1;
-                            }
+                            if (MODE == MODE_FROB && valid) part += dk;
                         }
                     }
                 }
@@ -673,9 +738,21 @@ static ApplyParams make_params(fft_geom g) {
     return P;
 }
 
-size_t apply_smem(fft_geom g) {
+size_t apply_smem(fft_geom g, int warps) {
     size_t tab = ((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15;
-    return tab + (size_t)APPLY_WARPS * STG_PER_WARP * sizeof(float4);
+    return tab + (size_t)warps * STG_PER_WARP * sizeof(float4);
+}
+
+size_t apply_smem(fft_geom g) { return apply_smem(g, APPLY_WARPS); }
+
+// Most warps (a multiple of 8, at most 24) one sharp-variant CTA can stage for.
+static int sharp_max_warps(fft_geom g) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int w = SHARP_MAX_WARPS;
+    while (w > APPLY_WARPS && apply_smem(g, w) > (size_t)optin) w -= 8;
+    return w;
 }
 
 template <int MODE, int DT, bool G, bool S, int PHI>
@@ -706,7 +783,7 @@ static fft_status set_attr_mode(size_t smem) {
 // Raise the dynamic shared-memory limit of every kernel instantiation once per geometry
 // (outside any stream capture), so launches need no attribute calls.
 fft_status set_apply_attributes(fft_geom g) {
-    const size_t smem = apply_smem(g);
+    const size_t smem = apply_smem(g, sharp_max_warps(g));
     fft_status rc;
     if ((rc = set_attr_mode<MODE_JT>(smem)) != FFT_OK) return rc;
     if ((rc = set_attr_mode<MODE_J>(smem)) != FFT_OK) return rc;
@@ -732,15 +809,47 @@ int apply_occupancy(fft_geom g) {
     return per_sm * sms;
 }
 
+// CTA shape of the sharp variants: the block of 8, 16 or 24 warps with the most resident
+// warps per SM (the smaller block on a tie), and the persistent grid that fills the GPU.
+void sharp_launch_shape(fft_geom g) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+    int best_w = APPLY_WARPS, best_b = 1, best_res = 0;
+    for (int w = APPLY_WARPS; w <= sharp_max_warps(g); w += 8) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, apply_kernel<MODE_JT, FFT_DT_STABLE, false, true, PHI_TABLE>,
+                                                      32 * w, apply_smem(g, w));
+        if (b * w > best_res) {
+            best_res = b * w;
+            best_w = w;
+            best_b = b;
+        }
+    }
+    cudaGetLastError();
+    g->sharp_warps = best_w;
+    g->sharp_ctas = std::max(best_b, 1) * sms;
+}
+
+// One apply launch: sharp single-column variants in the geometry's sharp CTA shape, the others
+// in 8-warp CTAs on the persistent grid.
+template <int MODE, int DT, bool G, bool S, int PHI>
+static void launch_apply(fft_geom g, const ApplyParams& P, cudaStream_t st) {
+    if (apply_sharp_wide<MODE, DT, S, PHI>()) {
+        apply_kernel<MODE, DT, G, S, PHI><<<g->sharp_ctas, 32 * g->sharp_warps, apply_smem(g, g->sharp_warps), st>>>(P);
+    } else {
+        apply_kernel<MODE, DT, G, S, PHI><<<g->apply_ctas, APPLY_THREADS, apply_smem(g), st>>>(P);
+    }
+}
+
 template <int MODE>
 static fft_status launch_mode(fft_geom g, const ApplyParams& P, cudaStream_t st) {
-    const size_t smem = apply_smem(g);
-    const int ctas = g->apply_ctas;
     FFT_CUDA(cudaMemsetAsync(g->counter, 0, sizeof(int32_t), st));
     if (g->n_items == 0) return FFT_OK;
     // MODE_COUNT evaluates no Phi: the table variant serves both representations
     constexpr int PHI_T = MODE == MODE_COUNT ? PHI_TABLE : PHI_TRIG;
-#define FFT_LAUNCH(DTV, GV, SV, PV) apply_kernel<MODE, DTV, GV, SV, PV><<<ctas, APPLY_THREADS, smem, st>>>(P)
+#define FFT_LAUNCH(DTV, GV, SV, PV) launch_apply<MODE, DTV, GV, SV, PV>(g, P, st)
 #define FFT_LAUNCH_GS(DTV, PV)                                      \
     do {                                                            \
         if (g->guard) {                                             \

@@ -141,7 +141,9 @@ struct fft_geom_s {
     int64_t evaluated = 0;
     double frob2 = -1.0;
     int64_t scratch_bytes = 0;
-    int apply_ctas = 0;                  // persistent grid of the apply kernels
+    int apply_ctas = 0;                  // persistent grid of the apply kernels (8-warp CTAs)
+    int sharp_warps = 8;                 // warps per CTA of the sharp-band single-column kernels
+    int sharp_ctas = 0;                  // their persistent grid
     int items_per_cta = 0;               // work-item granularity (autotuned or the default)
     // CG workspace (allocated on first use)
     float* cg_r = nullptr;               // [M] residual d - J m
@@ -177,6 +179,7 @@ fft_status compute_frob2(fft_geom g, double* out);
 fft_status set_apply_attributes(fft_geom g);
 int apply_occupancy(fft_geom g);
 size_t apply_smem(fft_geom g);
+void sharp_launch_shape(fft_geom g);
 int psf_tc_max_cols(fft_geom g);
 fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx, const float* d_val, int n_rhs,
                          const int32_t* col_map, float* out, cudaStream_t st);
