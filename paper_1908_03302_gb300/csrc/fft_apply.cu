@@ -4,12 +4,15 @@
 // Work decomposition
 //   * The voxel grid is cut into 16 x 16 x 8 tiles. Each tile has a list of candidate rows
 //     (built once per geometry by a conservative cull). A work item is a tile and a range of
-//     its rows; persistent CTAs pull items from a counter, heaviest first.
-//   * In a CTA, warp w owns a fixed 8 x 8 x 4 region of the tile (two 8 x 4 x 4 sub-bricks);
-//     lane l owns 4 consecutive x voxels of each sub-brick. All warps stream the item's rows
-//     independently: per chunk of 32 rows, lane l loads row l, moves its geometry into the
-//     tile's pair frame and tests it against the warp's two sub-bricks (tangent-plane bound
-//     of the convex detour); the survivors are staged in shared memory and broadcast.
+//     its rows; a unit is one of the tile's eight 8 x 8 x 4 regions (two 8 x 4 x 4
+//     sub-bricks) of one item, and every warp of the persistent grid pulls units from a
+//     counter, heaviest items first, on its own (the only CTA barrier follows the table load).
+//     CTAs have 8 warps (4 per SM for the 64-register variants); the sharp-band variants run
+//     in CTAs of 8, 16 or 24 warps, whichever keeps the most warps resident.
+//   * Lane l owns 4 consecutive x voxels of each sub-brick of its warp's region. Per chunk of
+//     32 rows, lane l loads row l, moves its geometry into the tile's pair frame and tests it
+//     against the region's two sub-bricks (tangent-plane bounds of the convex detour); the
+//     survivors are staged in shared memory and broadcast.
 //   * Per (row, voxel): pair-frame coordinates by FFMA from per-lane offsets, normalised
 //     detour (cancellation-free form), Phi from the band table in shared memory (one 64-bit
 //     load, linear interpolation), geometric factor 1 / (R_xs R_xr).
