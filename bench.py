@@ -46,7 +46,7 @@ FP32_LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) of one J^T on ring256 (the apply kernel and its slot reduction,
 # as timed), from the ncu capture summarised in profiles/apply_kernel_ring256.md; None until
 # captured for the current kernels.
-APPLY_TRAFFIC_BYTES = 352048896   # apply 87316224 + 109712896, jt_reduce 151964672 + 3055104
+APPLY_TRAFFIC_BYTES = 349024768   # apply 87322112 + 109116672, jt_reduce 151963392 + 622592
 
 
 def peaks():

@@ -66,3 +66,20 @@ def test_three_band_autotune(three_band):
     d = np.random.default_rng(10).normal(size=og.M)
     assert rel_l2(to_np(geo.J(to_dev(m))), og.J(m)) <= 1e-5
     assert rel_l2(to_np(geo.JT(to_dev(d))), og.JT(d)) <= 1e-5
+
+
+def test_single_sharp_band(fg):
+    # one 1.4 MHz band (sigma 0.2 MHz, Phi not zero at its cut-off): the sharp kernels in
+    # 8-warp CTAs, three per SM at 80 registers
+    base = wl.ring32()
+    w = wl.Workload("ring32_sharp", base.tx, base.pairs, np.zeros(len(base.pairs), np.int32),
+                    [wl.Band(1.4e6, 0.2e6)], base.grid, base.c0, cg_iters=6, lambda_rel=1e-3, model_seed=1,
+                    noise_seed=2)
+    og = oracle.Geometry.from_workload(w)
+    geo, _ = gpu_geometry(w)
+    m = wl.model_for(w)
+    d = np.random.default_rng(11).normal(size=og.M) * 1e-8
+    assert rel_l2(to_np(geo.J(to_dev(m))), og.J(m)) <= 1e-5
+    assert rel_l2(to_np(geo.JT(to_dev(d))), og.JT(d)) <= 1e-5
+    assert torch.equal(geo.JT(to_dev(d)), geo.JT(to_dev(d)))
+    assert abs(geo.support_evals - og.count_support()) <= 1e-4 * og.count_support()
