@@ -8,7 +8,7 @@
 //     sub-bricks) of one item, and every warp of the persistent grid pulls units from a
 //     counter, heaviest items first, on its own (the only CTA barrier follows the table load).
 //     CTAs have 8 warps (4 per SM for the 64-register variants); the sharp-band variants run
-//     in CTAs of 8, 16 or 24 warps, whichever keeps the most warps resident.
+//     in CTAs of 8 to 20 warps, whichever keeps the most warps resident.
 //   * Lane l owns 4 consecutive x voxels of each sub-brick of its warp's region. Per chunk of
 //     32 rows, lane l loads row l, moves its geometry into the tile's pair frame and tests it
 //     against the region's two sub-bricks (tangent-plane bounds of the convex detour); the
@@ -202,15 +202,17 @@ __device__ __noinline__ void sharp_fix(const ApplyParams& P, float4 A, float4 B,
                                             iy0, iz0, d);
 }
 
-// The sharp-band stable-detour table variants (single column) are built for CTAs of up to 24
-// warps at one per SM (at most 85 registers): as 8-warp CTAs three fit per SM on register
-// count, and where large band tables leave room for fewer, one CTA of 16 or 24 warps shares
-// one copy of the tables.
+// The sharp-band stable-detour table variants (single column) are built for CTAs of up to 20
+// warps at one per SM (96 registers used): one CTA of 20 warps shares one copy of the band
+// tables, and keeps more warps resident than 8-warp CTAs do (two per SM at this register
+// count, fewer where large tables fill shared memory). Measured against 24 warps at 80
+// registers and 16 warps at 128: the spills of the first and the lower occupancy of the
+// second cost more.
 template <int MODE, int DT, bool SHARP, int PHI>
 constexpr bool apply_sharp_wide() {
     return SHARP && DT == FFT_DT_STABLE && PHI == PHI_TABLE && MODE != MODE_JT4 && MODE != MODE_J4;
 }
-constexpr int SHARP_MAX_WARPS = 24;
+constexpr int SHARP_MAX_WARPS = 20;
 
 template <int MODE, int DT, bool GUARD, bool SHARP, int PHI>
 __global__ void __launch_bounds__(apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 32 * SHARP_MAX_WARPS : APPLY_THREADS,
@@ -762,7 +764,7 @@ static int sharp_max_warps(fft_geom g) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int w = SHARP_MAX_WARPS;
-    while (w > APPLY_WARPS && apply_smem(g, w) > (size_t)optin) w -= 8;
+    while (w > APPLY_WARPS && apply_smem(g, w) > (size_t)optin) w -= 4;
     return w;
 }
 
@@ -820,7 +822,7 @@ int apply_occupancy(fft_geom g) {
     return per_sm * sms;
 }
 
-// CTA shape of the sharp variants: the block of 8, 16 or 24 warps with the most resident
+// CTA shape of the sharp variants: the block of 8, 12, 16 or 20 warps with the most resident
 // warps per SM (the smaller block on a tie), and the persistent grid that fills the GPU.
 void sharp_launch_shape(fft_geom g) {
     int dev = 0, sms = 0;
@@ -828,7 +830,7 @@ void sharp_launch_shape(fft_geom g) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms < 1) sms = 1;
     int best_w = APPLY_WARPS, best_b = 1, best_res = 0;
-    for (int w = APPLY_WARPS; w <= sharp_max_warps(g); w += 8) {
+    for (int w = APPLY_WARPS; w <= sharp_max_warps(g); w += 4) {
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, apply_kernel<MODE_JT, FFT_DT_STABLE, false, true, PHI_TABLE>,
                                                       32 * w, apply_smem(g, w));

@@ -69,8 +69,8 @@ def test_three_band_autotune(three_band):
 
 
 def test_single_sharp_band(fg):
-    # one 1.4 MHz band (sigma 0.2 MHz, Phi not zero at its cut-off): the sharp kernels in
-    # 8-warp CTAs, three per SM at 80 registers
+    # one 1.4 MHz band (sigma 0.2 MHz, Phi not zero at its cut-off): the sharp kernels with
+    # one copy of a small table per SM
     base = wl.ring32()
     w = wl.Workload("ring32_sharp", base.tx, base.pairs, np.zeros(len(base.pairs), np.int32),
                     [wl.Band(1.4e6, 0.2e6)], base.grid, base.c0, cg_iters=6, lambda_rel=1e-3, model_seed=1,
