@@ -127,16 +127,15 @@ constexpr int apply_min_blocks() {
 // near the cut re-decides dt < dt_max in FP64. It returns in d[k] what the main pass's term
 // has to change by: val2 - val1 (J, J^T, four-column modes), |val2| - |val1| (coverage),
 // val2^2 - val1^2 (Frobenius), +1 / -1 (support count), 0 where nothing changes.
-// UNROLL: 8 when inlined (d stays in registers), 1 out of line.
-template <int MODE, int DT, bool GUARD, int PHI, int UNROLL>
-__device__ __forceinline__ void sharp_fix_body(const ApplyParams& P, float4 A, float4 B, float4 C, float Xl,
-                                               float Yl, float Zl, bool planar, bool inner0, bool inner1, float cutb,
-                                               uint32_t tb, float nm1, int nq, int ix0, int iy0, int iz0, float* d) {
+template <int MODE, int DT, bool GUARD, int PHI>
+__device__ __noinline__ void sharp_fix(const ApplyParams& P, float4 A, float4 B, float4 C, float Xl, float Yl,
+                                       float Zl, bool planar, bool inner0, bool inner1, float cutb, uint32_t tb,
+                                       float nm1, int nq, int ix0, int iy0, int iz0, float* d) {
     const float hx = B.x, hy = B.y, hz = B.z;
     const float hl = 0.5f * (A.x - A.y);
     const int b = __float_as_int(C.w) & 0xff;
     const double U = P.bc[b].U;
-#pragma unroll UNROLL
+#pragma unroll 1
     for (int k = 0; k < 8; ++k) {
         const int s = k >> 2, t = k & 3;
         d[k] = 0.0f;
@@ -184,22 +183,6 @@ __device__ __forceinline__ void sharp_fix_body(const ApplyParams& P, float4 A, f
         else if (MODE == MODE_FROB) d[k] = val2 * val2 - val1 * val1;
         else d[k] = val2 - val1;
     }
-}
-
-// Out of line for the modes where that measured faster (J, the set-up counts, the four-column
-// modes); J^T and the coverage keep it inline, where saving their eight live accumulators
-// around a call costs more than the registers it frees.
-template <int MODE>
-constexpr bool sharp_fix_outlined() {
-    return MODE != MODE_JT && MODE != MODE_COV;
-}
-
-template <int MODE, int DT, bool GUARD, int PHI>
-__device__ __noinline__ void sharp_fix(const ApplyParams& P, float4 A, float4 B, float4 C, float Xl, float Yl,
-                                       float Zl, bool planar, bool inner0, bool inner1, float cutb, uint32_t tb,
-                                       float nm1, int nq, int ix0, int iy0, int iz0, float* d) {
-    sharp_fix_body<MODE, DT, GUARD, PHI, 1>(P, A, B, C, Xl, Yl, Zl, planar, inner0, inner1, cutb, tb, nm1, nq, ix0,
-                                            iy0, iz0, d);
 }
 
 // The sharp-band stable-detour table variants (single column) are built for CTAs of up to 20
@@ -481,16 +464,10 @@ __global__ void __launch_bounds__(apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 32 
                     // FP64 re-decision of the voxels whose FP32 detour lies within CUT_BAND of
                     // the cut; d[k] is the change of this entry's term for voxel k = 4 s + t
                     float d[8];
-                    if (near) {
-                        if (sharp_fix_outlined<MODE>())
-                            sharp_fix<MODE, DT, GUARD, PHI>(P, A, B, C, Xl, Yl, Zl, planar, (i0 >> bit) & 1u,
-                                                            (i1 >> bit) & 1u, cutb, tb, nm1, nq, TX + oxi, TY + oyi,
-                                                            TZ + ozi, d);
-                        else
-                            sharp_fix_body<MODE, DT, GUARD, PHI, 8>(P, A, B, C, Xl, Yl, Zl, planar, (i0 >> bit) & 1u,
-                                                                    (i1 >> bit) & 1u, cutb, tb, nm1, nq, TX + oxi,
-                                                                    TY + oyi, TZ + ozi, d);
-                    }
+                    if (near)
+                        sharp_fix<MODE, DT, GUARD, PHI>(P, A, B, C, Xl, Yl, Zl, planar, (i0 >> bit) & 1u,
+                                                        (i1 >> bit) & 1u, cutb, tb, nm1, nq, TX + oxi, TY + oyi,
+                                                        TZ + ozi, d);
 #pragma unroll
                     for (int s = 0; s < 2; ++s) {
 #pragma unroll
