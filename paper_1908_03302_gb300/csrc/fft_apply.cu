@@ -111,9 +111,10 @@ __device__ __forceinline__ float detour_v64(const RowRec64& r, double ox, double
     return (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
 }
 
-// Resident CTAs per SM the register budget is sized for: the stable-detour table kernels fit
-// 64 registers without spilling (4 CTAs, 32 warps per SM); the others keep 80 (3 CTAs) and
-// the sharp-band ones 128 (2 CTAs).
+// Resident 8-warp CTAs per SM the register budget is sized for: the stable-detour table
+// kernels fit 64 registers without spilling (4 CTAs, 32 warps per SM); the others keep 80 (3
+// CTAs), the four-column ones and the other sharp-band ones 128 (2 CTAs). The single-column
+// sharp-band stable-detour table variants are sized separately (apply_sharp_wide below).
 template <int MODE, int DT, bool SHARP, int PHI>
 constexpr int apply_min_blocks() {
     return (SHARP || MODE == MODE_JT4 || MODE == MODE_J4) ? 2
