@@ -175,10 +175,12 @@ typedef struct {
  * fit or one fewer. The sizes are swept at the occupancy limit (stopping after two in a row
  * more than 2 % slower than the best), then the best size and its two neighbours with one CTA
  * per SM fewer: 2 to 9 candidates. Each runs J^T and J once timed (CUDA events on `stream`),
- * after one untimed pass unless the previous candidate's pair took over 20 ms,
- * and the fastest is kept (results do not depend on it beyond rounding of the split J^T
- * sums). Synchronous; allocates test vectors for the duration of the call; invalidates a
- * captured CG loop (the next fft_cg_solve captures again). info may be NULL.
+ * after one untimed pass unless the previous candidate's pair took over 20 ms, and the
+ * fastest is kept. Results do not depend on the choice beyond rounding of the split J^T sums.
+ * For geometries with a band whose Phi does not vanish at its cut-off, J and J^T run in one
+ * CTA of up to 20 warps per SM whatever the candidate; the CTA count then only sets the item
+ * granularity. Synchronous; allocates test vectors for the duration of the call; invalidates
+ * a captured CG loop (the next fft_cg_solve captures again). info may be NULL.
  */
 fft_status fft_geom_autotune(fft_geom g, void* stream, fft_tune_info_t* info);
 
