@@ -352,8 +352,12 @@ __global__ void __launch_bounds__(apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 32 
                 // The entry's evaluation, specialised for planar pairs (both transducers at one
                 // z: the axis has no z component, so h_z = 0 exactly and c1, c2 do not change
                 // along the lane's voxels or between the two sub-bricks).
-                auto entry_body = [&](auto planar_tag) {
+                // SH: the near-cut checks, only for rows of a band whose Phi does not vanish at
+                // the cut (the other rows of a sharp geometry take the plain evaluation; both
+                // give the same values there).
+                auto entry_body = [&](auto planar_tag, auto sharp_tag) {
                     constexpr bool PL = decltype(planar_tag)::value;
+                    constexpr bool SH = decltype(sharp_tag)::value;
                 const float off = PL ? fmaf(Xl, hx, Yl * hy) : fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
                 float psb = A.x + off, prb = A.y + off;
                 float c1 = PL ? fmaf(-Zl, hy, A.z) : fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 32 
                 const float c2t = (t == 0 ? c2 : fmaf(-ft, hz, c2));                               \
                 q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));                                         \
             }                                                                                      \
-            if (SHARP) {                                                                           \
+            if (SH) {                                                                              \
                 v = detour_v<DT, GUARD, INNER_V, true>(pst, prt, q2, hl, is, ir);                  \
                 near |= (fabsf(v - 1.0f) < cutb);                                                  \
                 v = __saturatef(v);                                                                \
@@ -456,10 +460,17 @@ __global__ void __launch_bounds__(apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 32 
                     }
                 }
                 };
-                if (planar)
-                    entry_body(std::true_type{});
-                else
-                    entry_body(std::false_type{});
+                if (SHARP && cutb > 0.0f) {
+                    if (planar)
+                        entry_body(std::true_type{}, std::integral_constant<bool, SHARP>{});
+                    else
+                        entry_body(std::false_type{}, std::integral_constant<bool, SHARP>{});
+                } else {
+                    if (planar)
+                        entry_body(std::true_type{}, std::false_type{});
+                    else
+                        entry_body(std::false_type{}, std::false_type{});
+                }
 #undef FFT_EVAL_SUB
                 if (SHARP && DT != FFT_DT_FP64 && __any_sync(0xffffffffu, near)) {
                     // FP64 re-decision of the voxels whose FP32 detour lies within CUT_BAND of
