@@ -197,3 +197,29 @@ def test_k0_zero_exactly_at_the_transducers():
         # a point 1 um away has a finite, non-zero value of at most the scale near the emitter
         x = xs + 1e-6 * (xr - xs) / np.linalg.norm(xr - xs)
         assert np.isfinite(oracle.k0(xs, xr, x, C0, tab, dtm))
+
+
+def test_multi_band_rows_use_their_own_band():
+    # Rows of band b use band b's table and cut-off (Sec. VI: measurements in several frequency
+    # bands): a two-band operator equals, row by row, the single-band operators, and its
+    # adjoint is the sum of theirs over each band's rows.
+    w = wl.tiny()
+    rows = w.row_pairs()
+    bor = (np.arange(len(rows)) % 2).astype(np.int32)
+    bands = [(1.0e6, 0.3e6), (1.4e6, 0.2e6)]
+    dtm = [3.0 / fc for fc, _ in bands]
+    tabs = [oracle.phi_table_gauss(fc, fs, 1024, d) for (fc, fs), d in zip(bands, dtm)]
+    two = oracle.Geometry(w.tx, rows, bor, tabs, dtm, w.grid, w.c0)
+    one = [oracle.Geometry(w.tx, rows, None, [tabs[b]], [dtm[b]], w.grid, w.c0) for b in range(2)]
+    rng = np.random.default_rng(21)
+    m = rng.normal(size=two.V)
+    d = rng.normal(size=two.M)
+    J2 = two.J(m)
+    for b in range(2):
+        sel = bor == b
+        assert np.array_equal(J2[sel], one[b].J(m)[sel])
+    ref = one[0].JT(np.where(bor == 0, d, 0.0)) + one[1].JT(np.where(bor == 1, d, 0.0))
+    assert np.max(np.abs(two.JT(d) - ref)) <= 1e-12 * np.max(np.abs(ref))
+    # the bands differ, so a mix-up of tables would show
+    J0, J1 = one[0].J(m), one[1].J(m)
+    assert np.linalg.norm(J0 - J1) > 0.1 * np.linalg.norm(J0)
