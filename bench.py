@@ -46,7 +46,7 @@ FP32_LANES_PER_SM_CLK = 128
 # DRAM bytes (read + write) of one J^T on ring256 (the apply kernel and its slot reduction,
 # as timed), from the ncu capture summarised in profiles/apply_kernel_ring256.md; None until
 # captured for the current kernels.
-APPLY_TRAFFIC_BYTES = 349024768   # apply 87322112 + 109116672, jt_reduce 151963392 + 622592
+APPLY_TRAFFIC_BYTES = 349740800   # apply 87283456 + 109496576, jt_reduce 151964672 + 996096
 
 
 def peaks():
