@@ -561,7 +561,9 @@ static double dot(const double* a, const double* b, int64_t n) {
  *         m += alpha p; r -= alpha q; s = J^T r - lambda m;
  *         gamma' = |s|^2; beta = gamma' / gamma; p = s + beta p
  * hist (nullable, n_iter + 1 values) receives gamma before each iteration and at the end.
- * Returns 0, or -4 if delta <= 0 or gamma is not finite.
+ * gamma = 0 means the gradient of the damped misfit vanishes at m: m is already its minimiser
+ * (the misfit is a convex quadratic), so the remaining iterations leave m unchanged and record
+ * gamma = 0. Returns 0, or -4 if delta <= 0 with a non-zero gradient or gamma is not finite.
  */
 int oracle_cgls(GEOM_ARGS, int64_t M, const double* dobs, double lambda, int32_t n_iter,
                 double* m, double* hist) {
@@ -578,9 +580,15 @@ int oracle_cgls(GEOM_ARGS, int64_t M, const double* dobs, double lambda, int32_t
     double gamma = dot(s, s, V);
     if (hist) hist[0] = gamma;
     for (int32_t it = 0; it < n_iter; ++it) {
+        if (!isfinite(gamma)) { status = -4; break; }
+        if (gamma == 0.0) {   /* converged: m minimises the damped misfit */
+            if (hist)
+                for (int32_t k = it + 1; k <= n_iter; ++k) hist[k] = 0.0;
+            break;
+        }
         oracle_J(tx, rows, band, tables, dt_max, n_tab, nx, ny, nz, h, org, c0, trig_dw, M, NULL, 0, p, q);
         double delta = dot(q, q, M) + lambda * dot(p, p, V);
-        if (!(delta > 0.0) || !isfinite(gamma)) { status = -4; break; }
+        if (!(delta > 0.0)) { status = -4; break; }
         double alpha = gamma / delta;
         for (int64_t v = 0; v < V; ++v) m[v] += alpha * p[v];
         for (int64_t i = 0; i < M; ++i) r[i] -= alpha * q[i];

@@ -66,9 +66,33 @@ def test_cgls_fixed_iterations_match_dense_cg(tiny):
     assert hist[0] == pytest.approx(b @ b, rel=1e-12)
 
 
-def test_cgls_breakdown_status(tiny):
+def test_cgls_zero_gradient_is_converged(tiny):
+    # d = 0 and m0 = 0: the gradient of the damped misfit vanishes, m = 0 is its minimiser
     w, geo, F = tiny
     m, hist, rc = geo.cgls(np.zeros(geo.M), 0.0, 3)
+    assert rc == 0
+    assert np.all(m == 0.0) and np.all(hist == 0.0)
+    # m0 = the damped solution itself: J^T (d - J m0) = lambda m0 up to rounding, so CGLS
+    # stays within rounding of it
+    rng = np.random.default_rng(23)
+    d = F @ rng.normal(size=geo.V)
+    lam = geo.lambda_abs(0.1)
+    ref = np.linalg.solve(F.T @ F + lam * np.eye(geo.V), F.T @ d)
+    m, hist, rc = geo.cgls(d, lam, 3, m0=ref)
+    assert rc == 0
+    assert np.linalg.norm(m - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_cgls_breakdown_status(tiny):
+    # a curvature |J p|^2 + lambda |p|^2 <= 0 (damping far below -|J|^2) or a non-finite
+    # datum is a breakdown
+    w, geo, F = tiny
+    rng = np.random.default_rng(24)
+    d = F @ rng.normal(size=geo.V)
+    m, hist, rc = geo.cgls(d, -1e3 * np.linalg.norm(F, 2) ** 2, 3)
+    assert rc == -4
+    d[5] = np.nan
+    m, hist, rc = geo.cgls(d, 0.0, 3)
     assert rc == -4
 
 
