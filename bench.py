@@ -1,16 +1,20 @@
 #!/usr/bin/env python3
 """Benchmark of the finite-frequency traveltime tomography hot path on GB300.
 
-Workload (default ``ring256``): 256 transducers on a 100 mm ring (32640 pairs), Gaussian
-spectrum 1 MHz / 0.4 MHz, 4096-sample Phi table to 3 us, 200 x 200 x 40 voxels at 1 mm,
-three nested cylinders, data = J dc + N(0, 5 ns), 30 CGLS iterations with relative damping
-1e-3. Synthetic, seeded inputs (the paper's lab dataset is not available).
+Workload (default ``slices3d``, the largest single-GPU configuration): the 256-element ring
+of radius 100 mm stepped to 16 z positions 4 mm apart (pairs only within a slice, 522240
+pairs), three frequency bands (0.6 / 1.0 / 1.4 MHz, sigma 0.2 MHz, one 4096-sample Phi table
+each, cut-off 3 periods), 1566720 rows, 256 x 256 x 96 voxels at 0.75 mm, 12 random
+ellipsoidal inclusions, data = J dc + N(0, 5 ns), 20 CGLS iterations with relative damping
+1e-3 replayed from a CUDA graph. ``--workload ring256`` runs the single-ring configuration
+(32640 pairs, 200 x 200 x 40 voxels at 1 mm, 30 iterations). Synthetic, seeded inputs (the
+paper's lab dataset is not available).
 
-One step = one damped least-squares solve (fft_cg_solve, 30 iterations) on resident data:
-(30 + 1) applications each of J and J^T, every entry rebuilt on the fly. The Phi table and
-the culled geometry are built once before timing (their build time is reported as
-``setup_ms``). The metric is in-support pair-voxel evaluations per second (J and J^T
-together); the roofline is that of the J^T kernel against the FP32 issue rate of the chip.
+One step = one damped least-squares solve (fft_cg_solve) on resident data: (n_iter + 1)
+applications each of J and J^T, every entry rebuilt on the fly. The Phi tables and the culled
+geometry are built once before timing (their build time is reported as ``setup_ms``). The
+metric is in-support pair-voxel evaluations per second (J and J^T together); the roofline is
+that of the J^T kernel against the FP32 issue rate of the chip.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 Under torchrun each rank runs its own replica (the path has no exchange step on one
@@ -43,10 +47,12 @@ UNIT = "eval/s"
 # 2 (index, fraction), 2 (lerp), 1 (rsqrt product), 1 (times Phi), 1 (accumulate).
 OPS_PER_EVAL = 24
 FP32_LANES_PER_SM_CLK = 128
-# DRAM bytes (read + write) of one J^T on ring256 (the apply kernel and its slot reduction,
-# as timed), from the ncu capture summarised in profiles/apply_kernel_ring256.md; None until
-# captured for the current kernels.
-APPLY_TRAFFIC_BYTES = 349740800   # apply 87283456 + 109496576, jt_reduce 151964672 + 996096
+# DRAM bytes (read + write) of one J^T (the apply kernel and its slot reduction, as timed) per
+# workload, from ncu captures of the current kernels (dram__bytes_read.sum +
+# dram__bytes_write.sum); a workload without a capture of the current build reports null.
+APPLY_TRAFFIC_BYTES = {
+    "ring256": 349740800,   # apply 87283456 + 109496576, jt_reduce 151964672 + 996096
+}
 
 
 def peaks():
@@ -260,8 +266,12 @@ def run_psf(args, ws, rank, local):
     k32 = min(len(spikes), args.psf_fp32_spikes)
     out_fp = torch.empty(k32 * len(subsets) * geo.V, device="cuda", dtype=torch.float32)
     fp_ms = timed(lambda: geo.psf_batch(spikes[:k32], subsets, mode=0, out=out_fp))
+    # the FP32 path with four columns per J^T (columns in spike-major order)
+    out_fp4 = torch.empty_like(out_fp)
+    fp4_ms = timed(lambda: geo.psf_batch(spikes[:k32], subsets, mode=2, out=out_fp4))
     tc = out_tc.view(len(subsets), len(spikes), geo.V)
     fp = out_fp.view(len(subsets), k32, geo.V)
+    fp4 = out_fp4.view(len(subsets), k32, geo.V)
     diff = []
     for sb in range(len(subsets)):
         for k in range(k32):
@@ -270,7 +280,7 @@ def run_psf(args, ws, rank, local):
                 diff.append(float((tc[sb, k].double() - fp[sb, k].double()).norm()) / nrm)
     # CPU baseline leg: the FP64 oracle on sampled voxels of a few PSFs (timed, and the same
     # values give the sampled error of both GPU paths)
-    errs_tc, errs_fp, cpu = [], [], None
+    errs_tc, errs_fp, errs_fp4, cpu = [], [], [], None
     if not args.no_cpu_baseline and rank == 0:
         import oracle
         og = oracle.Geometry.from_workload(w)
@@ -295,11 +305,13 @@ def run_psf(args, ws, rank, local):
                 vt = torch.as_tensor(vox, device="cuda")
                 errs_tc.append(float(np.linalg.norm(tc[sb, k][vt].double().cpu().numpy() - ref) / n))
                 errs_fp.append(float(np.linalg.norm(fp[sb, k][vt].double().cpu().numpy() - ref) / n))
+                errs_fp4.append(float(np.linalg.norm(fp4[sb, k][vt].double().cpu().numpy() - ref) / n))
         cpu = {"value": 1e3 * secs / n_vals * n_psf * geo.V, "unit": "ms", "cores": oracle.n_threads(),
                "kind": "oracle",
                "sample": f"FP64 oracle PSF values at {n_vals} voxels (2 spikes x subsets {{64, 256}}, within 20 "
                          f"voxels of the spike) in {secs:.1f} s, scaled linearly to {n_psf} PSFs x {geo.V} voxels"}
     fp_full_ms = fp_ms * len(spikes) / k32
+    fp4_full_ms = fp4_ms * len(spikes) / k32
     tc_avg = statistics.mean(tc_ms)
     info = geo.info()
     line = {
@@ -313,9 +325,13 @@ def run_psf(args, ws, rank, local):
                    "support_evals_per_apply": int(info.support_evals)},
         "fp32_path_ms_per_batch": fp_full_ms, "fp32_path_measured": f"{k32} spikes x 3 subsets, scaled",
         "speedup_tc_vs_fp32": fp_full_ms / tc_avg,
+        "fp32_batched_path_ms_per_batch": fp4_full_ms,
+        "fp32_batched_path": "four columns per J^T (fft_psf_batch mode 2), same spikes, scaled",
+        "speedup_tc_vs_fp32_batched": fp4_full_ms / tc_avg,
         "tensor": tensor,
         "tc_vs_fp32_rel_l2_max": max(diff) if diff else None,
         "err_vs_fp64_oracle": {"tc_rel_l2_max": max(errs_tc), "fp32_rel_l2_max": max(errs_fp),
+                               "fp32_batched_rel_l2_max": max(errs_fp4),
                                "sample": "2 spikes x subsets {64, 256}, <=256 voxels within 20 of the spike"}
         if errs_tc else None,
         "cpu_baseline": cpu,
@@ -464,7 +480,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="ring256",
+    ap.add_argument("--workload", default="slices3d",
                     choices=["ring32", "ring256", "ring256_3band", "slices3d", "psf3d", "spacing", "lowrank"])
     ap.add_argument("--lowrank-k", type=int, default=64)
     ap.add_argument("--psf-spikes", type=int, default=128)
@@ -531,7 +547,7 @@ def main():
 
     def step(mbuf):
         mbuf.zero_()
-        geo.cg_solve(d, w.lambda_rel, n_iter, m=mbuf)
+        geo.cg_solve(d, w.lambda_rel, n_iter, m=mbuf, check_status=False)   # asynchronous
 
     if args.mode == "apply":
         r0 = torch.randn(geo.M, device=dev, dtype=torch.float32) * 1e-8
@@ -590,6 +606,7 @@ def main():
         step(m)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    geo.cg_status()   # raises if a solve broke down
     barrier(ws)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(sum(step_ms), ws)
@@ -614,11 +631,11 @@ def main():
         jt_ms.append(a.elapsed_time(b))
         j_ms.append(c.elapsed_time(e))
     # the 2-D approximation (Eq. forward_2D) on the same geometry: the plane map and the
-    # kernel integrated over the grid's layers
+    # kernel integrated over the grid's layers (single-ring workloads only)
     j2_ms, jt2_ms = [], []
     m2 = torch.randn(geo.V2, device=dev, dtype=torch.float32)
     g2 = torch.empty(geo.V2, device=dev, dtype=torch.float32)
-    for i in range(3):
+    for i in range(3 if len(np.unique(w.tx[:, 2])) == 1 else 0):
         flush.fill_(float(i))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         c, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -639,15 +656,17 @@ def main():
     d_dev = torch.empty_like(d)
     m_dev = torch.empty_like(m)
     e2e_ms = []
-    for i in range(max(2, min(args.steps, 5))):
+    step_avg_ms = total_ms / args.steps
+    n_e2e = max(2, min(args.steps, 5 if step_avg_ms < 5000 else 3))
+    for i in range(n_e2e):
         flush.fill_(float(i))
         torch.cuda.synchronize()
         t_a = time.perf_counter()
         d_dev.copy_(d_host, non_blocking=True)
         m_dev.zero_()
-        geo.cg_solve(d_dev, w.lambda_rel, n_iter, m=m_dev)
+        geo.cg_solve(d_dev, w.lambda_rel, n_iter, m=m_dev, check_status=False)
         m_host.copy_(m_dev, non_blocking=True)
-        torch.cuda.synchronize()
+        geo.cg_status()
         e2e_ms.append(1e3 * (time.perf_counter() - t_a))
     e2e_total = max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws)
 
@@ -690,13 +709,13 @@ def main():
         "ms_per_J": 1e3 * j_avg, "ms_per_JT": 1e3 * jt_avg,
         "J_evals_per_s": support / j_avg, "JT_evals_per_s": support / jt_avg,
         "J_dense_equiv_per_s": geo.M * geo.V / j_avg, "JT_dense_equiv_per_s": geo.M * geo.V / jt_avg,
-        "ms_per_J2d": statistics.mean(j2_ms), "ms_per_JT2d": statistics.mean(jt2_ms),
+        "ms_per_J2d": statistics.mean(j2_ms) if j2_ms else None,
+        "ms_per_JT2d": statistics.mean(jt2_ms) if jt2_ms else None,
         "setup_ms": {"table": 1e3 * (t1 - t0), "geometry_and_cull": 1e3 * (t2 - t1), "autotune": 1e3 * (t3 - t2)},
         "autotune": tuning,
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
                      "frac": achieved / peak_evals,
-                     "traffic": APPLY_TRAFFIC_BYTES if (w.name == "ring256" and args.dt_mode == 0 and n_terms == 0)
-                     else None,
+                     "traffic": APPLY_TRAFFIC_BYTES.get(w.name) if (args.dt_mode == 0 and n_terms == 0) else None,
                      "kernel": "apply_kernel (J^T) + jt_reduce",
                      "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM_CLK} FP32 lanes x {sm_max:.0f} MHz "
                                    f"({pk_kind}) / {ops} ops per eval"},
@@ -704,7 +723,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": ws * evals_per_step / (e2e_total * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * geo.M, "d2h_bytes_per_step": 4 * geo.V,
-                "ms_per_step": e2e_total},
+                "ms_per_step": e2e_total, "steps": n_e2e},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }

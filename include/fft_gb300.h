@@ -290,24 +290,56 @@ fft_status fft_frob2(fft_geom g, double* out);
  *   d_dev     device float32[M] data.
  *   m_dev     device float32[V]: in = starting model (zeros for m0 = 0), out = solution.
  *   hist_host nullable host double[n_iter + 1]: |J^T r - lambda m|^2 before each iteration
- *             and after the last (the call then synchronises).
+ *             and after the last.
  * Vectors are FP32; inner products, alpha, beta and gamma are FP64 on the device (no host
  * round trip). The iteration loop is captured once per handle into a CUDA graph and
- * replayed. Returns FFT_ERR_BREAKDOWN (after synchronising) if a curvature was <= 0 or a
- * scalar became non-finite; the iterations after a breakdown leave m unchanged.
+ * replayed. A vanishing gradient (|J^T r - lambda m|^2 = 0) means m already minimises the
+ * misfit: the remaining iterations keep it, and that is not a breakdown.
+ * Asynchronous on `stream` when hist_host is NULL: the call returns once the solve is
+ * enqueued, and fft_cg_status gives its outcome. With hist_host the call synchronises and
+ * returns that outcome itself. The first solve on a handle also computes |J|_F^2
+ * (synchronously, then cached) and captures the graph.
  */
 fft_status fft_cg_solve(fft_geom g, const float* d_dev, double lambda_rel, int32_t n_iter,
                         float* m_dev, double* hist_host, void* stream);
 
 /*
+ * fft_cg_status - outcome of the last fft_cg_solve enqueued on g: synchronises `stream` (the
+ * solve's stream), then returns FFT_OK, or FFT_ERR_BREAKDOWN if a curvature was <= 0 with a
+ * non-zero gradient or a scalar became non-finite (the iterations after a breakdown leave m
+ * unchanged). FFT_OK if g has not solved yet. Each solve resets the flag, so the answer is for
+ * the most recent solve only.
+ */
+fft_status fft_cg_status(fft_geom g, void* stream);
+
+/*
  * fft_psf_batch - Hessian point-spread functions (Sec. II-D, Eq. resolution_2):
  *   out[(s * n_spike + k) * V + v] = sum_{p in S_s} J[p, v] J[p, spike_vox[k]]
  * i.e. H_S e_k with a unit (1 m/s) spike, for every row subset S_s and spike k.
- *   spike_vox     host int64[n_spike] voxel indices (0 <= . < V).
- *   subset_off    host int32[n_subsets + 1] CSR offsets into subset_rows.
- *   subset_rows   host int32[subset_off[n_subsets]] row indices (each subset ascending).
- *   mode          0: FP32 CUDA-core path.
+ *   spike_vox     host int64[n_spike] voxel indices (0 <= . < V), n_spike >= 1.
+ *   subset_off    host int32[n_subsets + 1] CSR offsets into subset_rows (subset_off[0] = 0,
+ *                 non-decreasing), n_subsets >= 1.
+ *   subset_rows   host int32[subset_off[n_subsets]] row indices in [0, M) (each subset ascending).
+ *   mode          0: FP32 CUDA cores, one PSF at a time: the column D = J_S e_k (one thread per
+ *                    row of S), then a J^T that skips the rows where D is zero.
+ *                 1: BF16 tensor cores: Y = J^T D for all n_subsets x n_spike columns of
+ *                    D = J_S E at once. D is built as sparse rows (FP32 values); one persistent
+ *                    kernel generates the J tile of each 8 x 4 x 4 voxel brick in FP32, rounds
+ *                    it and D to BF16 and issues tcgen05.mma (K = 32 rows per step, up to 512
+ *                    columns per launch; more columns run in blocks of spikes) accumulating
+ *                    in FP32 in tensor memory. Relative L2 error ~1e-3 (BF16 operands); the cut
+ *                    of a band whose Phi does not vanish at dt_max is taken in FP32 here (the
+ *                    FP32 paths re-decide it in FP64). At most 32 subsets; a subset must not
+ *                    list a row twice (FFT_ERR_ARG). FFT_ERR_TIMEOUT if a bounded wait on the
+ *                    tensor cores gave up.
+ *                 2: FP32 CUDA cores, four columns per J^T: the columns of D taken in
+ *                    (spike, subset) order, four at a time through the four-column J^T
+ *                    (fft_JT_apply_batch), so that rows shared by a spike's nested subsets
+ *                    are evaluated once. Same accuracy as mode 0.
  *   out_dev       device float32[n_subsets * n_spike * V], written entirely.
+ * Allocates its scratch (row lists, the columns of D, staging) with cudaMalloc on every call
+ * and synchronises with `stream` before returning; see fft_psf_noalloc for a variant that does
+ * neither allocation.
  */
 fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
                          const int32_t* subset_off, int32_t n_subsets,
@@ -323,12 +355,14 @@ fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
  *   rows_dev   DEVICE int32[n_rows]: the rows of S (any order). Indices outside [0, M) are
  *              skipped; the call then returns FFT_ERR_ARG after finishing.
  *   out_dev    device float32[V], written entirely: out[v] = sum_{p in S} J[p, v] J[p, spike_vox].
- * Scratch is a fixed array inside the library: 4,194,304 floats plus 256 bytes (about 16 MB),
- * held by every GPU that loads the library until the process exits. Geometries with more than
- * 4,194,304 rows are rejected with FFT_ERR_ARG. The first call on each device looks up the
- * array's device address, so make that first call before any stream capture. All calls share
- * the array (each clears what it uses); calls that overlap on the GPU race, so serialise them.
- * Synchronises with `stream` before returning.
+ * Scratch is a fixed array inside the library: 4,194,304 floats plus 256 bytes (about 16 MB).
+ * It is committed on a device when the first geometry is created there (fft_geom_create looks
+ * up its device address, which loads the module that holds it) and stays until the process
+ * exits; fft_psf_noalloc itself loads and allocates nothing. Geometries with more than
+ * 4,194,304 rows are rejected with FFT_ERR_ARG. All calls share the array (each clears what it
+ * uses); calls that overlap on the GPU race, so serialise them. The call copies an error
+ * counter to host memory and synchronises with `stream` before returning, so it must not be
+ * called while `stream` is being captured into a CUDA graph.
  */
 fft_status fft_psf_noalloc(fft_geom g, int64_t spike_vox, const int32_t* rows_dev, int32_t n_rows,
                            float* out_dev, void* stream);

@@ -286,7 +286,12 @@ class Geometry:
         check(_lib.load().fft_frob2(self.handle, ctypes.byref(v)))
         return v.value
 
-    def cg_solve(self, d, lambda_rel: float, n_iter: int, m=None, with_history: bool = False, stream=None):
+    def cg_solve(self, d, lambda_rel: float, n_iter: int, m=None, with_history: bool = False, stream=None,
+                 check_status: bool = True):
+        """CGLS on the damped normal equations (fft_cg_solve). The library call is asynchronous
+        without a history; check_status then waits for the solve (fft_cg_status) and raises
+        FFTError on a breakdown. check_status=False leaves the solve in flight: call
+        cg_status() later."""
         torch = _torch()
         if m is None:
             m = torch.zeros(self.V, device=d.device, dtype=torch.float32)
@@ -294,7 +299,13 @@ class Geometry:
         check(_lib.load().fft_cg_solve(self.handle, _dev_ptr(d, self.M, "d"), float(lambda_rel), int(n_iter),
                                        _dev_ptr(m, self.V, "m"), None if hist is None else hist.ctypes.data,
                                        _stream_handle(stream)))
+        if hist is None and check_status:
+            self.cg_status(stream)
         return (m, hist) if with_history else m
+
+    def cg_status(self, stream=None) -> None:
+        """Wait for the last solve on `stream` and raise FFTError if it broke down."""
+        check(_lib.load().fft_cg_status(self.handle, _stream_handle(stream)))
 
     def psf_batch(self, spikes: Sequence[int], subsets: Sequence[np.ndarray], mode: int = 0, out=None, stream=None):
         torch = _torch()

@@ -86,6 +86,7 @@ SIGNATURES = {
     "fft_lowrank_diag": (ctypes.c_int, [_VP, _VP, _VP, _I32, _D, _VP, _VP, _VP]),
     "fft_frob2": (ctypes.c_int, [_VP, ctypes.POINTER(_D)]),
     "fft_cg_solve": (ctypes.c_int, [_VP, _VP, _D, _I32, _VP, _VP, _VP]),
+    "fft_cg_status": (ctypes.c_int, [_VP, _VP]),
     "fft_psf_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP, _I32, _VP, _I32, _VP, _VP]),
     "fft_psf_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _I32, _VP, _VP]),
     "fft_tc_selftest": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_D)]),

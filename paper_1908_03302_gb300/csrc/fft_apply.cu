@@ -1002,7 +1002,6 @@ fft_status launch_JT(fft_geom g, const float* din, float* gout, cudaStream_t st)
     fft_status rc = launch_mode<MODE_JT>(g, P, st);
     if (rc != FFT_OK) return rc;
     return launch_jt_reduce<1>(g, g->gpart, gout, st);
-    return FFT_OK;
 }
 
 // cov_v = sum_p |J[p, v] w_p| (w null: all ones), gathered like J^T.
@@ -1013,7 +1012,6 @@ fft_status launch_cov(fft_geom g, const float* w, float* cov, cudaStream_t st) {
     fft_status rc = launch_mode<MODE_COV>(g, P, st);
     if (rc != FFT_OK) return rc;
     return launch_jt_reduce<1>(g, g->gpart, cov, st);
-    return FFT_OK;
 }
 
 // In-support evaluations (dt < dt_max) of one apply and evaluations actually performed.
@@ -1021,7 +1019,11 @@ fft_status count_support(fft_geom g, int64_t* support, int64_t* evaluated) {
     ApplyParams P = make_params(g);
     unsigned long long* d_cnt = nullptr;
     FFT_CUDA(cudaMalloc(&d_cnt, 2 * sizeof(unsigned long long)));
-    FFT_CUDA(cudaMemset(d_cnt, 0, 2 * sizeof(unsigned long long)));
+    cudaError_t e0 = cudaMemset(d_cnt, 0, 2 * sizeof(unsigned long long));
+    if (e0 != cudaSuccess) {
+        cudaFree(d_cnt);
+        return cuda_fail(e0, "count_support: cudaMemset");
+    }
     P.icount = d_cnt;
     fft_status rc = launch_mode<MODE_COUNT>(g, P, 0);
     unsigned long long h[2] = {0, 0};
@@ -1040,7 +1042,11 @@ fft_status compute_frob2(fft_geom g, double* out) {
     double* d_sum = nullptr;
     size_t n = (size_t)(g->n_items > 0 ? g->n_items : 1) * APPLY_WARPS;   // one per unit
     FFT_CUDA(cudaMalloc(&d_sum, n * sizeof(double)));
-    FFT_CUDA(cudaMemset(d_sum, 0, n * sizeof(double)));
+    cudaError_t e0 = cudaMemset(d_sum, 0, n * sizeof(double));
+    if (e0 != cudaSuccess) {
+        cudaFree(d_sum);
+        return cuda_fail(e0, "frob2: cudaMemset");
+    }
     P.dsum = d_sum;
     fft_status rc = launch_mode<MODE_FROB>(g, P, 0);
     std::vector<double> h(n, 0.0);

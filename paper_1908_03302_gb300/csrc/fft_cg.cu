@@ -62,7 +62,8 @@ __device__ double final_sum(const double* part, double* sh) {
     return block_reduce(s, sh);
 }
 
-// delta = |q|^2 + lambda |p|^2; alpha = gamma / delta, or breakdown.
+// delta = |q|^2 + lambda |p|^2; alpha = gamma / delta, or breakdown. gamma = 0 is a
+// vanishing gradient: m already minimises the damped misfit, alpha = 0 keeps it.
 __global__ void cg_alpha_kernel(double* __restrict__ scal, const double* __restrict__ part,
                                 int32_t* __restrict__ status) {
     __shared__ double sh[DOT_THREADS / 32];
@@ -72,7 +73,9 @@ __global__ void cg_alpha_kernel(double* __restrict__ scal, const double* __restr
         double delta = qq + scal[S_LAMBDA] * pp;
         double gamma = scal[S_GAMMA];
         scal[S_DELTA] = delta;
-        if (*status == 0 && delta > 0.0 && isfinite(delta) && isfinite(gamma)) {
+        if (*status == 0 && gamma == 0.0) {
+            scal[S_ALPHA] = 0.0;
+        } else if (*status == 0 && delta > 0.0 && isfinite(delta) && isfinite(gamma)) {
             scal[S_ALPHA] = gamma / delta;
         } else {
             scal[S_ALPHA] = 0.0;
@@ -270,10 +273,19 @@ extern "C" fft_status fft_cg_solve(fft_geom g, const float* d_dev, double lambda
     }
     FFT_CUDA(cudaGraphLaunch((cudaGraphExec_t)g->cg_graph, st));
     FFT_CUDA(cudaMemcpyAsync(m_dev, g->cg_m, sizeof(float) * g->V, cudaMemcpyDeviceToDevice, st));
+    if (!hist_host) return FFT_OK;   // asynchronous: fft_cg_status reports the outcome
+    FFT_CUDA(cudaMemcpyAsync(hist_host, g->cg_hist, sizeof(double) * (n_iter + 1), cudaMemcpyDeviceToHost, st));
+    return fft_cg_status(g, stream);
+}
+
+extern "C" fft_status fft_cg_status(fft_geom g, void* stream) {
+    FFT_ARG(g, "fft_cg_status: null handle");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    if (!g->cg_status) return FFT_OK;   // no solve yet
+    cudaStream_t st = (cudaStream_t)stream;
     int32_t status = 0;
     FFT_CUDA(cudaMemcpyAsync(&status, g->cg_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (hist_host)
-        FFT_CUDA(cudaMemcpyAsync(hist_host, g->cg_hist, sizeof(double) * (n_iter + 1), cudaMemcpyDeviceToHost, st));
     FFT_CUDA(cudaStreamSynchronize(st));
     if (status != 0) {
         set_error("fft_cg_solve: breakdown (non-positive curvature or non-finite scalar)");

@@ -184,4 +184,6 @@ int psf_tc_max_cols(fft_geom g);
 fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx, const float* d_val, int n_rhs,
                          const int32_t* col_map, float* out, cudaStream_t st);
 int64_t ceil_div(int64_t a, int64_t b);
+// Resolve (and so load) the no-allocation PSF's static scratch on device `dev` (current).
+fft_status noalloc_prepare(int dev);
 }  // namespace fftgb

@@ -554,10 +554,15 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     {
         int32_t* d_rc = nullptr;
         int32_t* d_cur = nullptr;
-        GEOM_CUDA(cudaMalloc(&d_rc, sizeof(int32_t) * n_rows));
-        GEOM_CUDA(cudaMalloc(&d_cur, sizeof(int32_t) * n_rows));
-        cudaMemset(d_rc, 0, sizeof(int32_t) * n_rows);
-        cudaMemset(d_cur, 0, sizeof(int32_t) * n_rows);
+        cudaError_t ea = cudaMalloc(&d_rc, sizeof(int32_t) * n_rows);
+        if (ea == cudaSuccess) ea = cudaMalloc(&d_cur, sizeof(int32_t) * n_rows);
+        if (ea == cudaSuccess) ea = cudaMemset(d_rc, 0, sizeof(int32_t) * n_rows);
+        if (ea == cudaSuccess) ea = cudaMemset(d_cur, 0, sizeof(int32_t) * n_rows);
+        if (ea != cudaSuccess) {
+            cudaFree(d_rc);
+            cudaFree(d_cur);
+        }
+        GEOM_CUDA(ea);
         if (g->E > 0) row_count_kernel<<<(unsigned)ceil_div(g->E, 256), 256>>>(g->tile_rows, g->E, d_rc);
         std::vector<int32_t> rc32(n_rows);
         cudaError_t e = cudaMemcpy(rc32.data(), d_rc, sizeof(int32_t) * n_rows, cudaMemcpyDeviceToHost);
@@ -582,6 +587,9 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
 
     // ---- work items
     GEOM_TRY(set_apply_attributes(g));
+    // commit the no-allocation PSF's static scratch on this device now, so that
+    // fft_psf_noalloc itself never loads a module or allocates
+    GEOM_TRY(noalloc_prepare(g->dev));
     g->apply_ctas = apply_occupancy(g);
     sharp_launch_shape(g);
     GEOM_TRY(dmalloc(g, &g->jpart, (size_t)g->E * APPLY_WARPS));

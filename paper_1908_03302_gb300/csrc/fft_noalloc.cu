@@ -8,11 +8,14 @@
 // fft_psf_noalloc computes the same quantity for one spike and one row subset with its
 // scratch in a file-scope device array of fixed size instead.
 //
-// The array (NOALLOC_MAX_ROWS floats plus a 256-byte header, about 16 MB) is part of the
-// library image: every GPU that loads the library holds it until the process exits. All
-// calls share it and it keeps the last call's contents; each call clears the part it uses
-// first. Calls that overlap on the GPU (different streams, or several host threads) race
-// on it and must be serialised by the caller.
+// The array (NOALLOC_MAX_ROWS floats plus a 256-byte header, about 16 MB) belongs to this
+// file's device module. With CUDA's lazy module loading that module, and the 16 MB, are
+// committed on a device the first time anything in it is used; fft_geom_create does that
+// (noalloc_prepare below), so the device memory is taken when the first geometry is created
+// on a device and held until the process exits, and fft_psf_noalloc itself loads and
+// allocates nothing. All calls share the array and it keeps the last call's contents; each
+// call clears the part it uses first. Calls that overlap on the GPU (different streams, or
+// several host threads) race on it and must be serialised by the caller.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -53,6 +56,30 @@ fft_status scratch_for_device(int dev, float** out) {
 }
 
 // D[rows[i]] = J[rows[i], v]; row indices outside [0, M) are counted in *err and skipped.
+template <int DT>
+__global__ void noalloc_column_kernel(const RowRec* __restrict__ rec, const int32_t* __restrict__ row_band,
+                                      const BandConst* __restrict__ bc, const float2* __restrict__ tab, int n_tab,
+                                      const int32_t* __restrict__ rows, int n, int64_t M, int nx, int ny,
+                                      int64_t v, const RowRec64* __restrict__ rec64, double3 org64, double h64,
+                                      float* __restrict__ D, unsigned int* __restrict__ err);
+
+}  // namespace
+
+// Look the array's device address up with `dev` current (the host-side symbol is only a
+// stand-in) and load the column kernels, so the first fft_psf_noalloc call on the device has
+// nothing left to load.
+fft_status noalloc_prepare(int dev) {
+    float* p = nullptr;
+    fft_status rc = scratch_for_device(dev, &p);
+    if (rc != FFT_OK) return rc;
+    cudaFuncAttributes fa;
+    FFT_CUDA(cudaFuncGetAttributes(&fa, noalloc_column_kernel<FFT_DT_STABLE>));
+    FFT_CUDA(cudaFuncGetAttributes(&fa, noalloc_column_kernel<FFT_DT_NAIVE>));
+    return FFT_OK;
+}
+
+namespace {
+
 template <int DT>
 __global__ void noalloc_column_kernel(const RowRec* __restrict__ rec, const int32_t* __restrict__ row_band,
                                       const BandConst* __restrict__ bc, const float2* __restrict__ tab, int n_tab,
@@ -131,7 +158,8 @@ extern "C" fft_status fft_psf_noalloc(fft_geom g, int64_t spike_vox, const int32
     FFT_CUDA(cudaMemcpyAsync(&bad, err, sizeof(bad), cudaMemcpyDeviceToHost, st));
     FFT_CUDA(cudaStreamSynchronize(st));
     if (bad) {
-        set_error("fft_psf_noalloc: " + std::to_string(bad) + " row indices were outside [0, n_rows) and skipped");
+        set_error("fft_psf_noalloc: " + std::to_string(bad) + " row indices were outside [0, M) (M = " +
+                  std::to_string(g->M) + ", the geometry's row count) and skipped");
         return FFT_ERR_ARG;
     }
     return FFT_OK;

@@ -216,6 +216,53 @@ fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, co
     return FFT_OK;
 }
 
+// FP32 path with the four-column J^T: the columns of D = J_S E are taken in (spike, subset)
+// order, so that a group of four mostly holds one spike's nested subsets and their rows are
+// evaluated once for all of them; each group is one column evaluation per member and one
+// four-column J^T into a staging block, copied to its outputs.
+fft_status psf_fp32_batched(fft_geom g, const int64_t* spike_vox, int32_t n_spike, const int32_t* subset_off,
+                            int32_t n_subsets, const int32_t* d_rows, float* out_dev, cudaStream_t st) {
+    float* D4 = nullptr;
+    float* Y4 = nullptr;
+    cudaError_t e = cudaMalloc(&D4, sizeof(float) * 4 * g->M);
+    if (e == cudaSuccess) e = cudaMalloc(&Y4, sizeof(float) * 4 * g->V);
+    fft_status rc = FFT_OK;
+    const int64_t n_cols = (int64_t)n_spike * n_subsets;
+    const double3 o64 = make_double3(g->grid.origin[0], g->grid.origin[1], g->grid.origin[2]);
+    for (int64_t c0 = 0; c0 < n_cols && e == cudaSuccess && rc == FFT_OK; c0 += 4) {
+        const int nc = (int)std::min<int64_t>(4, n_cols - c0);
+        e = cudaMemsetAsync(D4, 0, sizeof(float) * 4 * g->M, st);
+        for (int j = 0; j < nc && e == cudaSuccess; ++j) {
+            const int k = (int)((c0 + j) / n_subsets), s = (int)((c0 + j) % n_subsets);
+            const int32_t a = subset_off[s], n = subset_off[s + 1] - a;
+            if (n == 0) continue;
+            if (g->dt_mode == FFT_DT_NAIVE)
+                column_kernel<FFT_DT_NAIVE><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
+                    g->rec, g->row_band, g->d_band, g->tab, g->n_tab, d_rows + a, n, g->grid.nx, g->grid.ny,
+                    spike_vox[k], g->rec64, o64, g->grid.h, D4 + (int64_t)j * g->M);
+            else
+                column_kernel<FFT_DT_STABLE><<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(
+                    g->rec, g->row_band, g->d_band, g->tab, g->n_tab, d_rows + a, n, g->grid.nx, g->grid.ny,
+                    spike_vox[k], g->rec64, o64, g->grid.h, D4 + (int64_t)j * g->M);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) break;
+        if ((rc = launch_JT_batch(g, D4, 4, Y4, st)) != FFT_OK) break;
+        for (int j = 0; j < nc && e == cudaSuccess; ++j) {
+            const int k = (int)((c0 + j) / n_subsets), s = (int)((c0 + j) % n_subsets);
+            e = cudaMemcpyAsync(out_dev + ((int64_t)s * n_spike + k) * g->V, Y4 + (int64_t)j * g->V,
+                                sizeof(float) * g->V, cudaMemcpyDeviceToDevice, st);
+        }
+    }
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(D4);
+    cudaFree(Y4);
+    if (rc != FFT_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "fft_psf_batch (four-column FP32)");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "fft_psf_batch (four-column FP32) sync");
+    return FFT_OK;
+}
+
 }  // namespace
 
 extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
@@ -223,7 +270,8 @@ extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_
                                     int32_t mode, float* out_dev, void* stream) {
     FFT_ARG(g && spike_vox && subset_off && out_dev, "fft_psf_batch: null argument");
     FFT_ARG(n_spike >= 1 && n_subsets >= 1, "fft_psf_batch: need at least one spike and one subset");
-    FFT_ARG(mode == 0 || mode == 1, "fft_psf_batch: mode must be 0 (FP32) or 1 (BF16 tensor cores)");
+    FFT_ARG(mode >= 0 && mode <= 2,
+            "fft_psf_batch: mode must be 0 (FP32), 1 (BF16 tensor cores) or 2 (FP32, four columns per J^T)");
     FFT_ARG(mode == 0 || n_subsets <= 32, "fft_psf_batch: the tensor-core path takes at most 32 subsets");
     FFT_ARG(g->phi_kind == PHI_TABLE, "fft_psf_batch: needs a geometry built from sampled tables (not sine series)");
     fft_status rc = check_device(g->dev);
@@ -255,6 +303,14 @@ extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_
     if (n_idx > 0) e = cudaMemcpyAsync(d_rows, subset_rows, sizeof(int32_t) * n_idx, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && mode == 1) {
         rc = psf_tc_path(g, spike_vox, n_spike, subset_off, n_subsets, d_rows, out_dev, st);
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(d_rows);
+        if (rc != FFT_OK) return rc;
+        if (e2 != cudaSuccess) return cuda_fail(e2, "fft_psf_batch sync");
+        return FFT_OK;
+    }
+    if (e == cudaSuccess && mode == 2) {
+        rc = psf_fp32_batched(g, spike_vox, n_spike, subset_off, n_subsets, d_rows, out_dev, st);
         cudaError_t e2 = cudaStreamSynchronize(st);
         cudaFree(d_rows);
         if (rc != FFT_OK) return rc;

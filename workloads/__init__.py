@@ -280,6 +280,8 @@ def model_for(w: Workload) -> np.ndarray:
         return cylinders_model(w.grid)
     if w.name == "slices3d":
         return ellipsoids_model(w.grid, w.model_seed)
+    if w.name == "slices32":
+        return ellipsoids_model(w.grid, w.model_seed, semi_range=(3e-3, 8e-3), disc_radius=35e-3, z_half=12e-3)
     raise KeyError(w.name)
 
 
@@ -293,8 +295,22 @@ def ring256_3band() -> Workload:
                     lambda_rel=base.lambda_rel, model_seed=base.model_seed, noise_seed=base.noise_seed)
 
 
+def slices32() -> Workload:
+    """A small slice-by-slice acquisition of the slices3d kind: the 32-element 50 mm ring stepped
+    to 4 z positions 4 mm apart (pairs only within a slice), the three bands of slices3d
+    (0.6 / 1.0 / 1.4 MHz, sigma 0.2 MHz), 48 x 48 x 24 voxels at 2 mm, random ellipsoidal
+    inclusions, 20 CG iterations: 3 x 4 x 496 = 5952 rows, 55296 voxels."""
+    zpos = [-6e-3 + 4e-3 * s for s in range(4)]
+    tx, pairs = slice_rings(32, 50e-3, zpos)
+    bands = [Band(0.6e6, 0.2e6), Band(1.0e6, 0.2e6), Band(1.4e6, 0.2e6)]
+    bor = np.repeat(np.arange(3, dtype=np.int32), len(pairs))
+    return Workload("slices32", tx, pairs, bor, bands, Grid.centred(48, 48, 24, 2e-3), C0_WATER,
+                    cg_iters=20, lambda_rel=1e-3, model_seed=6, noise_seed=7)
+
+
 def by_name(name: str) -> Workload:
-    return {"ring32": ring32, "ring256": ring256, "slices3d": slices3d, "ring256_3band": ring256_3band}[name]()
+    return {"ring32": ring32, "ring256": ring256, "slices3d": slices3d, "ring256_3band": ring256_3band,
+            "slices32": slices32}[name]()
 
 
 def tiny(n_tx: int = 12, radius: float = 20e-3, n: Tuple[int, int, int] = (14, 14, 6),
