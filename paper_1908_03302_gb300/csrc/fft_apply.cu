@@ -198,9 +198,28 @@ constexpr bool apply_sharp_wide() {
 }
 constexpr int SHARP_MAX_WARPS = 20;
 
+// The plain stable-detour table variants (single column) keep the 64-register budget of four
+// 8-warp CTAs per SM but are built for blocks of up to 32 warps: where large (multi-band)
+// tables leave room for fewer than four 8-warp CTAs, one wide CTA shares one copy of the
+// tables and keeps 32 warps resident.
+template <int MODE, int DT, bool SHARP, int PHI>
+constexpr bool apply_plain_wide() {
+    return !SHARP && DT == FFT_DT_STABLE && PHI == PHI_TABLE && MODE != MODE_JT4 && MODE != MODE_J4;
+}
+constexpr int PLAIN_MAX_WARPS = 32;
+
+template <int MODE, int DT, bool SHARP, int PHI>
+constexpr int apply_block_bound() {
+    return apply_sharp_wide<MODE, DT, SHARP, PHI>()   ? 32 * SHARP_MAX_WARPS
+           : apply_plain_wide<MODE, DT, SHARP, PHI>() ? 32 * PLAIN_MAX_WARPS
+                                                      : APPLY_THREADS;
+}
+
 template <int MODE, int DT, bool GUARD, bool SHARP, int PHI>
-__global__ void __launch_bounds__(apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 32 * SHARP_MAX_WARPS : APPLY_THREADS,
-                                  apply_sharp_wide<MODE, DT, SHARP, PHI>() ? 1 : apply_min_blocks<MODE, DT, SHARP, PHI>())
+__global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
+                                  apply_block_bound<MODE, DT, SHARP, PHI>() == APPLY_THREADS
+                                      ? apply_min_blocks<MODE, DT, SHARP, PHI>()
+                                      : 1)
     apply_kernel(const __grid_constant__ ApplyParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* s_tab = reinterpret_cast<float2*>(smem);
@@ -782,10 +801,20 @@ static fft_status set_attr_mode(size_t smem) {
     return set_attr_one<MODE, FFT_DT_FP64, false, false, PHI_TABLE>(smem);
 }
 
+// Most warps (at most 32) one plain wide CTA can stage for.
+static int plain_max_warps(fft_geom g) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int w = PLAIN_MAX_WARPS;
+    while (w > APPLY_WARPS && apply_smem(g, w) > (size_t)optin) w -= 8;
+    return w;
+}
+
 // Raise the dynamic shared-memory limit of every kernel instantiation once per geometry
 // (outside any stream capture), so launches need no attribute calls.
 fft_status set_apply_attributes(fft_geom g) {
-    const size_t smem = apply_smem(g, sharp_max_warps(g));
+    const size_t smem = apply_smem(g, std::max(sharp_max_warps(g), plain_max_warps(g)));
     fft_status rc;
     if ((rc = set_attr_mode<MODE_JT>(smem)) != FFT_OK) return rc;
     if ((rc = set_attr_mode<MODE_J>(smem)) != FFT_OK) return rc;
@@ -834,33 +863,81 @@ void sharp_launch_shape(fft_geom g) {
     g->sharp_ctas = std::max(best_b, 1) * sms;
 }
 
-// One apply launch: sharp single-column variants in the geometry's sharp CTA shape, the others
-// in 8-warp CTAs on the persistent grid.
+// CTA shape of the plain stable-detour table variants: 8-warp CTAs on the (autotuned)
+// persistent grid, unless one wide CTA of 16, 24 or 32 warps keeps more warps resident per SM
+// (large multi-band tables), then one such CTA per SM.
+void plain_launch_shape(fft_geom g) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+    int b8 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, apply_kernel<MODE_JT, FFT_DT_STABLE, false, false, PHI_TABLE>,
+                                                  APPLY_THREADS, apply_smem(g));
+    int best_w = APPLY_WARPS, best_b = std::max(b8, 1), best_res = b8 * APPLY_WARPS;
+    for (int w = 2 * APPLY_WARPS; w <= plain_max_warps(g); w += APPLY_WARPS) {
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, apply_kernel<MODE_JT, FFT_DT_STABLE, false, false, PHI_TABLE>,
+                                                      32 * w, apply_smem(g, w));
+        if (b * w > best_res) {
+            best_res = b * w;
+            best_w = w;
+            best_b = b;
+        }
+    }
+    cudaGetLastError();
+    g->plain_warps = best_w;
+    g->plain_ctas = std::max(best_b, 1) * sms;
+}
+
+// One apply launch over P's items: sharp single-column variants in the geometry's sharp CTA
+// shape, plain stable-detour table variants in the plain shape, the others in 8-warp CTAs on
+// the persistent grid.
 template <int MODE, int DT, bool G, bool S, int PHI>
 static void launch_apply(fft_geom g, const ApplyParams& P, cudaStream_t st) {
     if (apply_sharp_wide<MODE, DT, S, PHI>()) {
         apply_kernel<MODE, DT, G, S, PHI><<<g->sharp_ctas, 32 * g->sharp_warps, apply_smem(g, g->sharp_warps), st>>>(P);
+    } else if (apply_plain_wide<MODE, DT, S, PHI>() && g->plain_warps > APPLY_WARPS) {
+        apply_kernel<MODE, DT, G, S, PHI><<<g->plain_ctas, 32 * g->plain_warps, apply_smem(g, g->plain_warps), st>>>(P);
     } else {
         apply_kernel<MODE, DT, G, S, PHI><<<g->apply_ctas, APPLY_THREADS, apply_smem(g), st>>>(P);
     }
 }
 
+// A sharp geometry's plain items (rows of bands whose Phi vanishes at the cut) run in the plain
+// variant, its sharp-band items in the sharp one: two launches, each pulling units from its own
+// counter. Other geometries run all items in one launch.
+template <int MODE, int DT, bool G, int PHI>
+static void launch_split(fft_geom g, const ApplyParams& P, cudaStream_t st) {
+    if (!g->sharp) {
+        launch_apply<MODE, DT, G, false, PHI>(g, P, st);
+        return;
+    }
+    const int np = g->n_items_plain, ns = g->n_items - g->n_items_plain;
+    if (np > 0) {
+        ApplyParams Q = P;
+        Q.n_items = np;
+        launch_apply<MODE, DT, G, false, PHI>(g, Q, st);
+    }
+    if (ns > 0) {
+        ApplyParams Q = P;
+        Q.items = P.items + np;
+        Q.n_items = ns;
+        Q.counter = P.counter + 1;
+        launch_apply<MODE, DT, G, true, PHI>(g, Q, st);
+    }
+}
+
 template <int MODE>
 static fft_status launch_mode(fft_geom g, const ApplyParams& P, cudaStream_t st) {
-    FFT_CUDA(cudaMemsetAsync(g->counter, 0, sizeof(int32_t), st));
+    FFT_CUDA(cudaMemsetAsync(g->counter, 0, 2 * sizeof(int32_t), st));
     if (g->n_items == 0) return FFT_OK;
     // MODE_COUNT evaluates no Phi: the table variant serves both representations
     constexpr int PHI_T = MODE == MODE_COUNT ? PHI_TABLE : PHI_TRIG;
-#define FFT_LAUNCH(DTV, GV, SV, PV) launch_apply<MODE, DTV, GV, SV, PV>(g, P, st)
 #define FFT_LAUNCH_GS(DTV, PV)                                      \
     do {                                                            \
-        if (g->guard) {                                             \
-            if (g->sharp) FFT_LAUNCH(DTV, true, true, PV);          \
-            else FFT_LAUNCH(DTV, true, false, PV);                  \
-        } else {                                                    \
-            if (g->sharp) FFT_LAUNCH(DTV, false, true, PV);         \
-            else FFT_LAUNCH(DTV, false, false, PV);                 \
-        }                                                           \
+        if (g->guard) launch_split<MODE, DTV, true, PV>(g, P, st);  \
+        else launch_split<MODE, DTV, false, PV>(g, P, st);          \
     } while (0)
     if (g->phi_kind == PHI_TRIG) {   // geometry creation guarantees dt_mode STABLE
         FFT_LAUNCH_GS(FFT_DT_STABLE, PHI_T);
@@ -868,11 +945,10 @@ static fft_status launch_mode(fft_geom g, const ApplyParams& P, cudaStream_t st)
         FFT_LAUNCH_GS(FFT_DT_STABLE, PHI_TABLE);
     } else if (g->dt_mode == FFT_DT_NAIVE) {
         FFT_LAUNCH_GS(FFT_DT_NAIVE, PHI_TABLE);
-    } else {
-        FFT_LAUNCH(FFT_DT_FP64, false, false, PHI_TABLE);
+    } else {   // FP64 detour: the cut is decided in FP64 everywhere, one plain launch
+        launch_apply<MODE, FFT_DT_FP64, false, false, PHI_TABLE>(g, P, st);
     }
 #undef FFT_LAUNCH_GS
-#undef FFT_LAUNCH
     FFT_CUDA(cudaGetLastError());
     return FFT_OK;
 }

@@ -144,6 +144,12 @@ struct fft_geom_s {
     int apply_ctas = 0;                  // persistent grid of the apply kernels (8-warp CTAs)
     int sharp_warps = 8;                 // warps per CTA of the sharp-band single-column kernels
     int sharp_ctas = 0;                  // their persistent grid
+    int plain_warps = 8;                 // warps per CTA of the plain stable-detour table kernels
+    int plain_ctas = 0;                  // their persistent grid when plain_warps > 8
+    // Sharp geometries split each tile's entries: rows of bands whose Phi vanishes at the cut
+    // first, then rows of sharp bands; items never mix the two, the plain items come first.
+    std::vector<int64_t> tile_nplain;    // host: plain entries of each tile (empty: no split)
+    int32_t n_items_plain = 0;           // items [0, n_items_plain) hold plain rows only
     int items_per_cta = 0;               // work-item granularity (autotuned or the default)
     // CG workspace (allocated on first use)
     float* cg_r = nullptr;               // [M] residual d - J m
@@ -180,6 +186,7 @@ fft_status set_apply_attributes(fft_geom g);
 int apply_occupancy(fft_geom g);
 size_t apply_smem(fft_geom g);
 void sharp_launch_shape(fft_geom g);
+void plain_launch_shape(fft_geom g);
 int psf_tc_max_cols(fft_geom g);
 fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx, const float* d_val, int n_rhs,
                          const int32_t* col_map, float* out, cudaStream_t st);

@@ -60,42 +60,75 @@ __device__ __forceinline__ bool tile_keeps_row(const CullParams& C, int T, int64
     return false;
 }
 
-__global__ void tile_count_kernel(const CullParams C, int64_t* __restrict__ cnt) {
-    __shared__ int64_t sh[CULL_THREADS / 32];
+// Kept rows of tile T (cnt), and of those the rows of bands that are not sharp (cnt_plain,
+// nullable; counted only when `split`).
+__global__ void tile_count_kernel(const CullParams C, int split, int64_t* __restrict__ cnt,
+                                  int64_t* __restrict__ cnt_plain) {
+    __shared__ int64_t sh[2][CULL_THREADS / 32];
     const int T = blockIdx.x;
-    int64_t c = 0;
-    for (int64_t p = threadIdx.x; p < C.M; p += CULL_THREADS) c += tile_keeps_row(C, T, p) ? 1 : 0;
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+    int64_t c = 0, cp = 0;
+    for (int64_t p = threadIdx.x; p < C.M; p += CULL_THREADS) {
+        if (tile_keeps_row(C, T, p)) {
+            ++c;
+            if (split && !C.bc[C.row_band[p]].sharp) ++cp;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        cp += __shfl_xor_sync(0xffffffffu, cp, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = c;
+        sh[1][threadIdx.x >> 5] = cp;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int64_t s = 0;
-        for (int w = 0; w < CULL_THREADS / 32; ++w) s += sh[w];
+        int64_t s = 0, sp = 0;
+        for (int w = 0; w < CULL_THREADS / 32; ++w) {
+            s += sh[0][w];
+            sp += sh[1][w];
+        }
         cnt[T] = s;
+        if (cnt_plain) cnt_plain[T] = sp;
     }
 }
 
-// Writes the kept rows of tile T in ascending row order.
+// Writes the kept rows of tile T in ascending row order; with `split` (nplain given) the rows of
+// bands that are not sharp first (from off[T]) and the rows of sharp bands after them (from
+// off[T] + nplain[T]), each part in ascending row order.
 __global__ void tile_fill_kernel(const CullParams C, const int64_t* __restrict__ off,
-                                 int32_t* __restrict__ rows) {
-    __shared__ int wsum[CULL_THREADS / 32];
+                                 const int64_t* __restrict__ nplain, int32_t* __restrict__ rows) {
+    __shared__ int wsum[2][CULL_THREADS / 32];
     const int T = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int64_t base = off[T];
+    int64_t base0 = off[T], base1 = nplain ? off[T] + nplain[T] : off[T + 1];
     for (int64_t p0 = 0; p0 < C.M; p0 += CULL_THREADS) {
         const int64_t p = p0 + threadIdx.x;
         const bool keep = p < C.M && tile_keeps_row(C, T, p);
-        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) wsum[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, total = 0;
-        for (int w = 0; w < CULL_THREADS / 32; ++w) {
-            if (w < warp) before += wsum[w];
-            total += wsum[w];
+        const bool sharp = keep && nplain && C.bc[C.row_band[p]].sharp;
+        const uint32_t bal0 = __ballot_sync(0xffffffffu, keep && !sharp);
+        const uint32_t bal1 = __ballot_sync(0xffffffffu, sharp);
+        if (lane == 0) {
+            wsum[0][warp] = __popc(bal0);
+            wsum[1][warp] = __popc(bal1);
         }
-        const int64_t pos = base + before + __popc(bal & ((1u << lane) - 1u));
-        if (keep && pos < off[T + 1]) rows[pos] = (int32_t)p;
-        base += total;
+        __syncthreads();
+        int before0 = 0, total0 = 0, before1 = 0, total1 = 0;
+        for (int w = 0; w < CULL_THREADS / 32; ++w) {
+            if (w < warp) {
+                before0 += wsum[0][w];
+                before1 += wsum[1][w];
+            }
+            total0 += wsum[0][w];
+            total1 += wsum[1][w];
+        }
+        const uint32_t below = (1u << lane) - 1u;
+        if (keep) {
+            const int64_t pos = sharp ? base1 + before1 + __popc(bal1 & below) : base0 + before0 + __popc(bal0 & below);
+            if (pos < off[T + 1]) rows[pos] = (int32_t)p;
+        }
+        base0 += total0;
+        base1 += total1;
         __syncthreads();
     }
 }
@@ -218,28 +251,36 @@ fft_status build_items(fft_geom g, const std::vector<int64_t>& toff, int items_p
     const int64_t target = (int64_t)items_per_cta * g->apply_ctas;
     int64_t ch = std::max<int64_t>(64, ceil_div(std::max<int64_t>(g->E, 1), std::max<int64_t>(target, 1)));
     ch = ceil_div(ch, 32) * 32;
-    std::vector<Item> items;
+    // plain rows [toff, toff + nplain) and sharp-band rows [toff + nplain, toff1) of a split
+    // geometry go to different items; the tile's slots number its plain items first
+    const bool split = !g->tile_nplain.empty();
+    std::vector<Item> items, items_sharp;
     std::vector<int32_t> slot0(g->n_tiles, -2), nslot(g->n_tiles, 0);
     int32_t slots = 0;
     for (int64_t T = 0; T < g->n_tiles; ++T) {
         const int64_t n = toff[T + 1] - toff[T];
         if (n == 0) continue;
-        const int64_t k = ceil_div(n, ch);
+        const int64_t np = split ? g->tile_nplain[T] : n;
+        const int64_t kp = ceil_div(np, ch), ks = ceil_div(n - np, ch), k = kp + ks;
         if (k == 1) {
-            items.push_back(Item{(int32_t)T, -1, toff[T], toff[T + 1]});
+            (kp == 1 ? items : items_sharp).push_back(Item{(int32_t)T, -1, toff[T], toff[T + 1]});
             slot0[T] = -1;
         } else {
             slot0[T] = slots;
             nslot[T] = (int32_t)k;
             for (int64_t q = 0; q < k; ++q) {
-                const int64_t a = toff[T] + q * ch, b = std::min(toff[T + 1], a + ch);
-                items.push_back(Item{(int32_t)T, slots + (int32_t)q, a, b});
+                const int64_t lo = q < kp ? toff[T] : toff[T] + np, hi = q < kp ? toff[T] + np : toff[T + 1];
+                const int64_t a = lo + (q < kp ? q : q - kp) * ch, b = std::min(hi, a + ch);
+                (q < kp ? items : items_sharp).push_back(Item{(int32_t)T, slots + (int32_t)q, a, b});
             }
             slots += (int32_t)k;
         }
     }
-    std::stable_sort(items.begin(), items.end(),
-                     [](const Item& x, const Item& y) { return (x.e1 - x.e0) > (y.e1 - y.e0); });
+    auto heavier = [](const Item& x, const Item& y) { return (x.e1 - x.e0) > (y.e1 - y.e0); };
+    std::stable_sort(items.begin(), items.end(), heavier);
+    std::stable_sort(items_sharp.begin(), items_sharp.end(), heavier);
+    g->n_items_plain = (int32_t)items.size();
+    items.insert(items.end(), items_sharp.begin(), items_sharp.end());
     if (g->items) {   // the buffers below are replaced: take them out of the scratch count
         g->scratch_bytes -= (int64_t)(sizeof(Item) * g->n_items + 2 * sizeof(int32_t) * g->n_tiles +
                                       sizeof(float) * (size_t)g->n_slots * TILE_VOX);
@@ -510,21 +551,40 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     C.tiles_y = g->tiles[1];
 
     std::vector<int64_t> tcnt(g->n_tiles), toff(g->n_tiles + 1, 0);
+    // sharp geometries keep each tile's plain rows ahead of its sharp-band rows, so that the
+    // two kinds run in separate launches (the plain kernels need fewer registers)
+    const bool split = g->sharp;
+    int64_t* d_nplain = nullptr;
     {
         int64_t* d_cnt = nullptr;
         GEOM_TRY(dmalloc(g, &g->tile_off, g->n_tiles + 1));
         d_cnt = g->tile_off;   // counts first, offsets after
-        tile_count_kernel<<<(unsigned)g->n_tiles, CULL_THREADS>>>(C, d_cnt);
-        GEOM_CUDA(cudaGetLastError());
-        GEOM_CUDA(cudaMemcpy(tcnt.data(), d_cnt, sizeof(int64_t) * g->n_tiles, cudaMemcpyDeviceToHost));
+        if (split) GEOM_CUDA(cudaMalloc(&d_nplain, sizeof(int64_t) * g->n_tiles));
+        tile_count_kernel<<<(unsigned)g->n_tiles, CULL_THREADS>>>(C, split ? 1 : 0, d_cnt, d_nplain);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpy(tcnt.data(), d_cnt, sizeof(int64_t) * g->n_tiles, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && split) {
+            g->tile_nplain.resize(g->n_tiles);
+            e = cudaMemcpy(g->tile_nplain.data(), d_nplain, sizeof(int64_t) * g->n_tiles, cudaMemcpyDeviceToHost);
+        }
         for (int64_t T = 0; T < g->n_tiles; ++T) toff[T + 1] = toff[T] + tcnt[T];
         g->E = toff[g->n_tiles];
-        GEOM_CUDA(cudaMemcpy(g->tile_off, toff.data(), sizeof(int64_t) * (g->n_tiles + 1), cudaMemcpyHostToDevice));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(g->tile_off, toff.data(), sizeof(int64_t) * (g->n_tiles + 1), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) cudaFree(d_nplain);
+        GEOM_CUDA(e);
     }
-    GEOM_TRY(dmalloc(g, &g->tile_rows, g->E));
-    if (g->E > 0) {
-        tile_fill_kernel<<<(unsigned)g->n_tiles, CULL_THREADS>>>(C, g->tile_off, g->tile_rows);
-        GEOM_CUDA(cudaGetLastError());
+    {
+        fft_status r2 = dmalloc(g, &g->tile_rows, g->E);
+        if (r2 == FFT_OK && g->E > 0) {
+            tile_fill_kernel<<<(unsigned)g->n_tiles, CULL_THREADS>>>(C, g->tile_off, d_nplain, g->tile_rows);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) r2 = cuda_fail(e, "tile lists");
+        }
+        cudaFree(d_nplain);
+        GEOM_TRY(r2);
     }
 
     // ---- FP64 pair-frame bases of the entries
@@ -592,6 +652,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     GEOM_TRY(noalloc_prepare(g->dev));
     g->apply_ctas = apply_occupancy(g);
     sharp_launch_shape(g);
+    plain_launch_shape(g);
     GEOM_TRY(dmalloc(g, &g->jpart, (size_t)g->E * APPLY_WARPS));
     GEOM_TRY(dmalloc(g, &g->counter, 4));
     GEOM_TRY(build_items(g, toff, DEFAULT_ITEMS_PER_CTA));
