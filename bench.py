@@ -485,7 +485,7 @@ def main():
     ap.add_argument("--lowrank-k", type=int, default=64)
     ap.add_argument("--psf-spikes", type=int, default=128)
     ap.add_argument("--psf-fp32-spikes", type=int, default=8)
-    ap.add_argument("--psf-geometry", default="slices3d", choices=["slices3d", "ring256"])
+    ap.add_argument("--psf-geometry", default="slices3d", choices=["slices3d", "ring256", "ring256_3band"])
     ap.add_argument("--psf-tc-only", action="store_true", help="time only the tensor-core path (profiling)")
     ap.add_argument("--dt-mode", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

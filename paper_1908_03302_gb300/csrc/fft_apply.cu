@@ -924,6 +924,7 @@ static void launch_split(fft_geom g, const ApplyParams& P, cudaStream_t st) {
         Q.items = P.items + np;
         Q.n_items = ns;
         Q.counter = P.counter + 1;
+        if (Q.dsum) Q.dsum = P.dsum + (size_t)np * 8;   // per-unit partials follow the plain launch's
         launch_apply<MODE, DT, G, true, PHI>(g, Q, st);
     }
 }

@@ -6,20 +6,26 @@
 // for an 8 x 4 x 4 sub-brick (128 voxels = the MMA's M) the rows whose support reaches it are
 // the contraction dimension K and the (subset, spike) columns are N.
 //
-// Per CTA (one per SM; 16 generator warps and one MMA warp) and sub-brick:
-//   1. scan the tile's candidate rows, keep those that may reach the sub-brick (tangent-plane
-//      bound of the convex detour), stage their pair-frame data in shared memory;
-//   2. for every chunk of 32 kept rows, generator warp w owns rows 2w and 2w + 1: it clears the
-//      sparse D entries it wrote into the chunk's B buffer three chunks earlier, scatters the
-//      rows' D entries (BF16), generates its two rows of the A tile J[p, v] (FP32 evaluation as
-//      in the J^T kernel, rounded to BF16) and arrives on the buffer's "full" mbarrier; the MMA
-//      warp waits for it, issues tcgen05.mma (M = 128, N = up to 2 x 256, K = 32) accumulating
-//      in TMEM and commits to the buffer's "empty" mbarrier, which the generators wait for
-//      before they reuse the buffer. Three A / B buffers and no CTA-wide barrier per chunk let
-//      generation run up to three chunks ahead of the tensor cores;
-//   3. after the last chunk, TMEM -> registers -> Y.
-// Every wait is bounded; a thread whose wait timed out sets a status word and waits no more,
-// and the CTA stops at the end of the sub-brick.
+// One persistent CTA per SM runs a pipeline of three warp roles over units (tile, sub-brick):
+//   * 4 scan warps test the tile's candidate rows against the sub-brick (tangent-plane bound
+//     of the convex detour; rows without D entries are dropped), 32 candidates per warp and
+//     block, and append the kept rows' pair-frame records to a ring of 8 chunks of 32 rows in
+//     shared memory, in candidate order (the blocks take turns), so the K order is fixed.
+//     A chunk is published with a header (unit, rows, first / last of the unit) on its
+//     "ring full" mbarrier;
+//   * 16 generator warps take the chunks in order: warp w loads the D entries of rows 2w and
+//     2w + 1, generates those two rows of the A tile J[p, v] (FP32 evaluation as in the J^T
+//     kernel, rounded to BF16), scatters the rows' D entries (BF16) into the chunk's B tile and
+//     arrives on the stage's "full" mbarrier; after the last chunk of a unit they move the
+//     accumulator TMEM -> registers -> Y and arrive on "TMEM free";
+//   * 1 MMA warp waits for "full", issues tcgen05.mma (M = 128, N = up to 2 x 256, K = 32;
+//     the unit's first chunk starts a new accumulation, after "TMEM free") and commits to the
+//     stage's "done" mbarrier; one chunk later it waits for those MMAs, clears the stage's B
+//     tile (dense 16-byte stores) and arrives on "empty", which the generators wait for before
+//     reusing the stage.
+// Three A / B stages and the 8-chunk row ring decouple the roles: no CTA-wide barrier between
+// the first and the last unit. Every wait is bounded; a thread whose wait timed out sets a
+// status word and leaves its loop, so that the others time out in turn and the CTA ends.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -36,15 +42,17 @@ namespace fftgb {
 
 namespace {
 
-constexpr int GEN_WARPS = 16;          // warps that generate J and scatter D
-constexpr int TC_WARPS = GEN_WARPS + 1;    // + one warp that issues the MMAs
+constexpr int GEN_WARPS = 16;          // warps that generate J and scatter D (warps 0 .. 15)
+constexpr int SCAN_WARPS = 4;          // warps that scan candidate rows (warps 16 .. 19)
+constexpr int MMA_WARP = GEN_WARPS + SCAN_WARPS;   // the warp that issues the MMAs
+constexpr int TC_WARPS = MMA_WARP + 1;
 constexpr int TC_THREADS = TC_WARPS * 32;
 constexpr int KC = 32;                 // rows per chunk (MMA K per chunk): 2 per generator warp
-constexpr int NSTAGE = 3;              // A / B buffers in the ring
-constexpr int SEG = TC_THREADS;        // tile entries scanned per pass (one per thread)
-constexpr int LIST_CAP = SEG + KC;     // kept rows waiting for a chunk (staged records)
+constexpr int NSTAGE = 3;              // A / B stages
+constexpr int RING = 8;                // chunks of staged rows between the scan and the generation
 constexpr int D_LANES = 16;            // lanes that scatter one row's D entries
 constexpr long long WAIT_BUDGET = 4000000000ll;   // cycles (~2 s)
+constexpr int HDR_FIRST = 1, HDR_LAST = 2;         // chunk header flags
 
 struct PsfTcParams {
     const RowRec* rec;
@@ -76,12 +84,31 @@ struct PsfTcParams {
     unsigned long long* chunks;   // chunks (128 x 32 A tiles) issued, summed over CTAs
 };
 
+struct ChunkHdr {
+    int unit;     // (tile << 4) | sub-brick; n_rows < 0 ends the CTA's work
+    int n_rows;   // staged rows in the chunk (0 .. KC)
+    int flags;    // HDR_FIRST, HDR_LAST
+    int pad;
+};
+
 struct TcShared {
-    unsigned long long full[NSTAGE];    // generator warps -> MMA warp (GEN_WARPS arrivals)
-    unsigned long long empty[NSTAGE];   // MMA warp -> generator warps (tcgen05.commit)
+    unsigned long long full[NSTAGE];       // generator warps -> MMA warp (GEN_WARPS arrivals)
+    unsigned long long done[NSTAGE];       // tensor cores -> MMA warp and epilogue (tcgen05.commit)
+    unsigned long long empty[NSTAGE];      // MMA warp -> generator warps (B tile cleared; 32 arrivals)
+    unsigned long long ring_full[RING];    // scan warps -> generator and MMA warps (1 arrival)
+    unsigned long long ring_empty[RING];   // generator and MMA warps -> scan warps (GEN_WARPS + 1)
+    unsigned long long tmem_free;          // epilogue read the accumulator -> MMA warp (GEN_WARPS)
+    unsigned long long unit_done;          // scan warps finished a unit (SCAN_WARPS arrivals)
+    unsigned long long unit_ready;         // scan warp 0 fetched the next unit (1 arrival)
+    ChunkHdr hdr[RING];
+    BandConst bc[MAX_BANDS];
     uint32_t tmem_slot;
-    int unit;
-    int wcnt[TC_WARPS];
+    int scan_unit;                         // unit index being scanned (>= n_units: no more)
+    int turn;                              // next block of 32 candidates allowed to append
+    int p_chunk;                           // producer: global index of the chunk being filled
+    int p_fill;                            // its staged rows
+    int p_first;                           // it is the first chunk of the current unit
+    int p_started;                         // the current unit has staged rows
 };
 
 __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
@@ -97,15 +124,50 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+__device__ __forceinline__ void st_volatile(int* p, int v) { *reinterpret_cast<volatile int*>(p) = v; }
+
+// Every lane of the warp waits (bounded) for the phase of `mbar` with the given parity, so each
+// one acquires what the arrivals released. Returns false, for the whole warp, if some lane's
+// wait timed out (status set).
+__device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, int lane, int32_t* status) {
+    const bool ok = wait_phase(mbar, parity);
+    if (!ok) atomicExch(status, FFT_ERR_TIMEOUT);
+    (void)lane;
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Producer side, called by the scan warp that holds the turn (whole warp): publish chunk
+// `chunk` (lane 0 writes the header and arrives on its "ring full" barrier).
+__device__ __forceinline__ void publish_chunk(TcShared& S, uint32_t ring_full0, int chunk, int unit, int n_rows,
+                                              int flags, int lane) {
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) {
+        ChunkHdr& h = S.hdr[chunk % RING];
+        h.unit = unit;
+        h.n_rows = n_rows;
+        h.flags = flags;
+        tc::mbar_arrive(ring_full0 + 8u * (uint32_t)(chunk % RING));
+    }
+    __syncwarp();
+}
+
+// Before the first row of chunk `chunk` is staged, its ring slot must have been released by
+// the consumers of chunk - RING.
+__device__ __forceinline__ bool ring_slot_free(uint32_t ring_empty0, int chunk, int lane, int32_t* status) {
+    if (chunk < RING) return true;
+    return warp_wait(ring_empty0 + 8u * (uint32_t)(chunk % RING), (uint32_t)(((chunk / RING) - 1) & 1), lane, status);
+}
+
 // GUARD: some voxel centre lies on a transducer (the geometry's flag): the guarded detour.
 template <bool GUARD>
 __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_constant__ PsfTcParams P) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ TcShared S;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool is_gen = warp < GEN_WARPS;
 
-    // ---- shared-memory carve-up: A[NSTAGE], B[NSTAGE] (1 KB aligned), table, staged row list
+    // ---- shared-memory carve-up: A[NSTAGE], B[NSTAGE] (1 KB aligned), tables, row ring
     const uint32_t a_bytes = 128u * KC * 2u;
     const uint32_t b_bytes = (uint32_t)P.b_rows * KC * 2u;
     unsigned char* sA0 = smem;
@@ -113,16 +175,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
     size_t off = NSTAGE * (size_t)a_bytes + NSTAGE * (size_t)b_bytes;
     float2* s_tab = reinterpret_cast<float2*>(smem + off);
     off += ((size_t)P.n_bands * P.n_tab * sizeof(float2) + 15) & ~(size_t)15;
-    float4* s_stg = reinterpret_cast<float4*>(smem + off);          // [LIST_CAP][3] staged kept rows
+    float4* s_ring = reinterpret_cast<float4*>(smem + off);   // [RING][KC][3] staged rows
 
     for (int i = tid; i < P.n_bands * P.n_tab; i += TC_THREADS) s_tab[i] = P.tab[i];
-    {   // B buffers start cleared; afterwards each generator lane clears the entries it wrote
+    if (tid < P.n_bands) S.bc[tid] = P.bc[tid];
+    {   // B stages start cleared; afterwards the MMA warp clears each one after its MMAs
         uint4* b4 = reinterpret_cast<uint4*>(sB0);
         for (uint32_t i = tid; i < NSTAGE * b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
     }
     const uint32_t tab_addr = smem_addr(s_tab);
     const float nm1 = (float)(P.n_tab - 1);
-    const uint32_t full0 = smem_addr(&S.full[0]), empty0 = smem_addr(&S.empty[0]);
+    const uint32_t full0 = smem_addr(&S.full[0]), empty0 = smem_addr(&S.empty[0]), done0 = smem_addr(&S.done[0]);
+    const uint32_t ring_full0 = smem_addr(&S.ring_full[0]), ring_empty0 = smem_addr(&S.ring_empty[0]);
+    const uint32_t tmem_free = smem_addr(&S.tmem_free);
+    const uint32_t unit_done = smem_addr(&S.unit_done), unit_ready = smem_addr(&S.unit_ready);
     if (warp == 0) {
         tc::tmem_alloc(smem_addr(&S.tmem_slot), (uint32_t)P.tmem_cols);
         tc::tmem_relinquish();
@@ -130,80 +196,89 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
     if (tid == 0) {
         for (int b = 0; b < NSTAGE; ++b) {
             tc::mbar_init(full0 + 8u * b, GEN_WARPS);
-            tc::mbar_init(empty0 + 8u * b, 1);
+            tc::mbar_init(done0 + 8u * b, 1);
+            tc::mbar_init(empty0 + 8u * b, 32);
         }
+        for (int b = 0; b < RING; ++b) {
+            tc::mbar_init(ring_full0 + 8u * b, 1);
+            tc::mbar_init(ring_empty0 + 8u * b, GEN_WARPS + 1);
+        }
+        tc::mbar_init(tmem_free, GEN_WARPS);
+        tc::mbar_init(unit_done, SCAN_WARPS);
+        tc::mbar_init(unit_ready, 1);
+        S.p_chunk = 0;
+        S.p_fill = 0;
+        S.p_first = 1;
+        S.p_started = 0;
+        S.turn = 0;
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    __syncthreads();   // the only CTA-wide barrier before the teardown
     tc::fence_after_sync();
     const uint32_t taddr = S.tmem_slot;
-    const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)P.n_half);
-
-    int chunk = 0;        // chunks issued by this CTA so far (selects buffer and mbarrier phases)
     bool failed = false;
-    // Generation role: warp w evaluates rows 2w and 2w + 1 of a chunk; lane l owns the four
-    // consecutive x voxels (4 lx + t, ly, lz), t = 0..3, of the 8 x 4 x 4 sub-brick, with
-    // lx = l & 1, ly = (l >> 1) & 3, lz = l >> 3. Voxel t of lane l is MMA row (TMEM lane)
-    // m = 32 t + l, which spreads a warp's stores over all eight 16-byte slots of a core matrix.
-    // For D the warp owns B-tile rows 2w (lanes 0-15) and 2w + 1 (lanes 16-31) of every buffer;
-    // lane i of a half scatters the row's D entries i and i + 16 (more, rarely, in a loop).
-    const int glx = lane & 1, gly = (lane >> 1) & 3, glz = lane >> 3;
-    const int d_r = 2 * warp + (lane >> 4), d_i0 = lane & (D_LANES - 1);
-    // D positions this lane wrote into the buffer of the current chunk, of the next one and of
-    // the one after (the buffers rotate with the chunks): (j0 + 1) | (j1 + 1) << 10, bit 20 if
-    // the row had more than 2 D_LANES entries (then the lane clears its whole share of the row)
-    uint32_t old0 = 0, old1 = 0, old2 = 0;
+    int chunk = 0;   // chunks this warp has consumed (generator and MMA warps)
 
-    for (;;) {
-        __syncthreads();   // everyone has read the previous unit index before it is replaced
-        if (tid == 0) S.unit = atomicAdd(P.counter, 1);
-        __syncthreads();
-        const int unit = S.unit;
-        if (unit >= P.n_units || failed) break;
-        const int T = P.units[unit] >> 4, sb = P.units[unit] & 15;
-        const int tx = T % P.tiles_x, ty = (T / P.tiles_x) % P.tiles_y, tz = T / (P.tiles_x * P.tiles_y);
-        // sub-brick origin in the tile (8 x 4 x 4 bricks: 2 along x, 4 along y, 2 along z)
-        const int SX = 8 * (sb & 1), SY = 4 * ((sb >> 1) & 3), SZ = 4 * (sb >> 3);
-        const int X0 = TILE_X * tx + SX, Y0 = TILE_Y * ty + SY, Z0 = TILE_Z * tz + SZ;
-        if (X0 >= P.nx || Y0 >= P.ny || Z0 >= P.nz) continue;   // uniform across the CTA
-        const int64_t e_begin = P.tile_off[T], e_end = P.tile_off[T + 1];
-        // this lane's first voxel, relative to the tile origin (generation)
-        const float Xv = (float)(SX + 4 * glx), Yv = (float)(SY + gly), Zv = (float)(SZ + glz);
-        int n_list = 0, head = 0, unit_chunks = 0;
-
-        for (int64_t seg = e_begin; seg < e_end; seg += SEG) {
-            // ---- 1. scan: keep rows that may reach the sub-brick, staged in the row list;
-            //         the rows left over from the previous pass move to the front first
-            __syncthreads();   // every warp is done with the list entries of earlier chunks
-            if (head > 0) {
-                const int carry = n_list - head;
-                float4 c0, c1, c2;
-                if (tid < carry) {
-                    c0 = s_stg[(head + tid) * 3 + 0];
-                    c1 = s_stg[(head + tid) * 3 + 1];
-                    c2 = s_stg[(head + tid) * 3 + 2];
+    if (warp >= GEN_WARPS && warp < MMA_WARP) {
+        // ================= scan warps: candidate rows -> staged records in the row ring
+        const int k = warp - GEN_WARPS;
+        for (int u = 0;; ++u) {
+            if (k == 0) {
+                if (u > 0) {
+                    // every scan warp has appended its blocks of the previous unit: close it
+                    failed = failed || !warp_wait(unit_done, (uint32_t)((u - 1) & 1), lane, P.status);
+                    __threadfence_block();
+                    if (!failed && S.p_started) {
+                        const int pc = S.p_chunk, pf = S.p_fill;
+                        // a unit whose rows filled its last chunk exactly gets an empty closing chunk
+                        if (pf == 0) failed = failed || !ring_slot_free(ring_empty0, pc, lane, P.status);
+                        if (!failed)
+                            publish_chunk(S, ring_full0, pc, P.units[S.scan_unit], pf,
+                                          HDR_LAST | (S.p_first ? HDR_FIRST : 0), lane);
+                        __syncwarp();
+                        if (lane == 0) {
+                            S.p_chunk = pc + 1;
+                            S.p_fill = 0;
+                        }
+                    }
                 }
-                __syncthreads();
-                if (tid < carry) {
-                    s_stg[tid * 3 + 0] = c0;
-                    s_stg[tid * 3 + 1] = c1;
-                    s_stg[tid * 3 + 2] = c2;
+                __syncwarp();
+                if (lane == 0) {
+                    S.scan_unit = failed ? P.n_units : atomicAdd(P.counter, 1);
+                    S.turn = 0;
+                    S.p_first = 1;
+                    S.p_started = 0;
+                    __threadfence_block();
+                    tc::mbar_arrive(unit_ready);
                 }
-                n_list = carry;
-                head = 0;
+                __syncwarp();
+            } else {
+                failed = failed || !warp_wait(unit_ready, (uint32_t)(u & 1), lane, P.status);
             }
-            {
-                const int64_t e = seg + tid;
+            __threadfence_block();
+            const int unit = failed ? P.n_units : S.scan_unit;
+            if (unit >= P.n_units) break;
+            const int ucode = P.units[unit];
+            const int T = ucode >> 4, sb = ucode & 15;
+            const int tx = T % P.tiles_x, ty = (T / P.tiles_x) % P.tiles_y, tz = T / (P.tiles_x * P.tiles_y);
+            const int X0 = TILE_X * tx + 8 * (sb & 1), Y0 = TILE_Y * ty + 4 * ((sb >> 1) & 3),
+                      Z0 = TILE_Z * tz + 4 * (sb >> 3);
+            const bool inside = X0 < P.nx && Y0 < P.ny && Z0 < P.nz;
+            const int64_t e_begin = P.tile_off[T], e_end = P.tile_off[T + 1];
+            const int n_blocks = inside ? (int)((e_end - e_begin + 31) / 32) : 0;
+            for (int b = k; b < n_blocks && !failed; b += SCAN_WARPS) {
+                // ---- test this block's 32 candidates (no ordering needed yet)
+                const int64_t e = e_begin + 32 * (int64_t)b + lane;
                 bool keep = false;
-                float4 s0, s1, s2;
+                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
                 if (e < e_end) {
                     const int p = P.tile_rows[e];
                     const int64_t d0 = P.d_off[p], d1 = P.d_off[p + 1];
                     if (d1 > d0) {   // rows without D entries add nothing
                         const RowRec r = P.rec[p];
-                        const int b = P.row_band[p];
-                        const BandConst bc = P.bc[b];
+                        const int bnd = P.row_band[p];
+                        const BandConst bc = S.bc[bnd];
                         const float hb = bc.h;
                         const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
                         const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
@@ -215,7 +290,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                             const float pext = 3.5f * hb * fabsf(ex) + 1.5f * hb * (fabsf(ey) + fabsf(ez)) + 1e-3f;
                             const bool inner = fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl;
                             // table base (a multiple of 8) with the inner / planar flags in bits 0, 1
-                            const uint32_t tb = (tab_addr + (uint32_t)(b * P.n_tab) * 8u - MAGIC_BITS_X8) |
+                            const uint32_t tb = (tab_addr + (uint32_t)(bnd * P.n_tab) * 8u - MAGIC_BITS_X8) |
                                                 (inner ? 1u : 0u) | (ez == 0.0f ? 2u : 0u);
                             s0 = P.ebase[e];
                             s1 = make_float4(hb * ex, hb * ey, hb * ez, P.ebase3[e]);
@@ -225,79 +300,137 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                     }
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-                if (lane == 0) S.wcnt[warp] = __popc(bal);
-                __syncthreads();
-                int before = 0, total = 0;
-#pragma unroll
-                for (int w = 0; w < TC_WARPS; ++w) {
-                    const int c = S.wcnt[w];
-                    before += (w < warp) ? c : 0;
-                    total += c;
-                }
-                if (keep) {
-                    const int pos = n_list + before + __popc(bal & ((1u << lane) - 1u));
-                    s_stg[pos * 3 + 0] = s0;
-                    s_stg[pos * 3 + 1] = s1;
-                    s_stg[pos * 3 + 2] = s2;
-                }
-                n_list += total;
-                __syncthreads();
-            }
-            const bool last_seg = seg + SEG >= e_end;
-            // ---- 2. chunks of KC kept rows: no CTA-wide barrier, only the two mbarrier rings
-            while (n_list - head >= KC || (last_seg && n_list - head > 0)) {
-                const int nrows = min(KC, n_list - head);
-                const int buf = chunk % NSTAGE;
-                const uint32_t use = (uint32_t)(chunk / NSTAGE);   // use count of this buffer
-                unsigned char* sA = sA0 + buf * a_bytes;
-                unsigned char* sB = sB0 + buf * b_bytes;
-                if (is_gen) {
-                    const float4* stg = s_stg + (size_t)head * 3;
-                    if (chunk >= NSTAGE && !failed) {   // the MMAs that last read this buffer must be done
-                        if (!wait_phase(empty0 + 8u * buf, (use - 1u) & 1u)) {
-                            if (lane == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
-                            failed = true;
+                // ---- wait for this block's turn, then append its kept rows in lane order
+                bool ok = true;
+                {   // back off while waiting, so that the spin does not take issue slots from the
+                    // generator warps on this SM sub-partition
+                    const long long t0 = clock64();
+                    while (ld_volatile(&S.turn) != b) {
+                        __nanosleep(64);
+                        if (clock64() - t0 > WAIT_BUDGET) {
+                            atomicExch(P.status, FFT_ERR_TIMEOUT);
+                            ok = false;
+                            break;
                         }
                     }
-                    // D entries of this lane's B row: loads issued now, stored after the generation
-                    uint32_t d_beg = 0;
-                    int d_cnt = 0;
-                    if (d_r < nrows) {
-                        const float4 C = stg[d_r * 3 + 2];
-                        d_beg = __float_as_uint(C.z);
-                        d_cnt = __float_as_int(C.w);
+                }
+                failed = failed || !__all_sync(0xffffffffu, ok);
+                if (failed) break;
+                __threadfence_block();
+                const int n = __popc(bal);
+                if (n > 0) {
+                    int pc = S.p_chunk;
+                    const int pf = S.p_fill;
+                    // the slots the rows go to must be free: the current chunk's (if it starts
+                    // here) and the next one's (if the rows spill over)
+                    if (pf == 0) failed = failed || !ring_slot_free(ring_empty0, pc, lane, P.status);
+                    if (pf + n > KC) failed = failed || !ring_slot_free(ring_empty0, pc + 1, lane, P.status);
+                    if (failed) break;
+                    if (keep) {
+                        const int pos = pf + __popc(bal & ((1u << lane) - 1u));
+                        const int cc = pc + pos / KC, rr = pos % KC;
+                        float4* dst = s_ring + ((size_t)(cc % RING) * KC + rr) * 3;
+                        dst[0] = s0;
+                        dst[1] = s1;
+                        dst[2] = s2;
                     }
-                    const bool has0 = d_i0 < d_cnt, has1 = d_i0 + D_LANES < d_cnt;
-                    uint32_t j0 = 0, j1 = 0;
-                    float dv0 = 0.0f, dv1 = 0.0f;
-                    if (has0) {
-                        j0 = P.d_idx[d_beg + d_i0];
-                        dv0 = P.d_val[d_beg + d_i0];
+                    int nf = pf + n;
+                    const int first = S.p_first;
+                    if (nf >= KC) {   // the chunk is full: publish it
+                        publish_chunk(S, ring_full0, pc, ucode, KC, first ? HDR_FIRST : 0, lane);
+                        ++pc;
+                        nf -= KC;
                     }
-                    if (has1) {
-                        j1 = P.d_idx[d_beg + d_i0 + D_LANES];
-                        dv1 = P.d_val[d_beg + d_i0 + D_LANES];
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (pf + n >= KC) S.p_first = 0;
+                        S.p_chunk = pc;
+                        S.p_fill = nf;
+                        S.p_started = 1;
                     }
-                    // generate A: rows 2 warp, 2 warp + 1; this lane's four voxels
-                    float vals[2][NX_LANE];
+                }
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) st_volatile(&S.turn, b + 1);
+            }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(unit_done);
+        }
+        if (k == 0 && !failed) {   // no more units: tell the consumers
+            const int pc = S.p_chunk;
+            if (ring_slot_free(ring_empty0, pc, lane, P.status)) publish_chunk(S, ring_full0, pc, 0, -1, 0, lane);
+        }
+    } else if (warp < GEN_WARPS) {
+        // ================= generator warps
+        // Warp w evaluates rows 2w and 2w + 1 of a chunk; lane l owns the four consecutive x
+        // voxels (4 lx + t, ly, lz), t = 0..3, of the 8 x 4 x 4 sub-brick, with lx = l & 1,
+        // ly = (l >> 1) & 3, lz = l >> 3. Voxel t of lane l is MMA row (TMEM lane) m = 32 t + l,
+        // which spreads a warp's stores over all eight 16-byte slots of a core matrix. For D the
+        // warp owns B-tile rows 2w (lanes 0-15) and 2w + 1 (lanes 16-31) of every stage; lane i
+        // of a half scatters the row's D entries i, i + 16, i + 32, ...
+        const int glx = lane & 1, gly = (lane >> 1) & 3, glz = lane >> 3;
+        const int d_r = 2 * warp + (lane >> 4), d_i0 = lane & (D_LANES - 1);
+        for (;; ++chunk) {
+            const int slot = chunk % RING;
+            if (!warp_wait(ring_full0 + 8u * slot, (uint32_t)((chunk / RING) & 1), lane, P.status)) {
+                failed = true;
+                break;
+            }
+            const ChunkHdr h = S.hdr[slot];
+            if (h.n_rows < 0) break;
+            const int nrows = h.n_rows;
+            const int T = h.unit >> 4, sb = h.unit & 15;
+            const int SX = 8 * (sb & 1), SY = 4 * ((sb >> 1) & 3), SZ = 4 * (sb >> 3);
+            const float4* stg = s_ring + (size_t)slot * KC * 3;
+            const int buf = chunk % NSTAGE;
+            const uint32_t use = (uint32_t)(chunk / NSTAGE);
+            unsigned char* sA = sA0 + buf * a_bytes;
+            unsigned char* sB = sB0 + buf * b_bytes;
+            // D entries of this lane's B row: loads issued now, stored after the generation
+            uint32_t d_beg = 0;
+            int d_cnt = 0;
+            if (d_r < nrows) {
+                const float4 C = stg[d_r * 3 + 2];
+                d_beg = __float_as_uint(C.z);
+                d_cnt = __float_as_int(C.w);
+            }
+            const bool has0 = d_i0 < d_cnt, has1 = d_i0 + D_LANES < d_cnt;
+            uint32_t j0 = 0, j1 = 0;
+            float dv0 = 0.0f, dv1 = 0.0f;
+            if (has0) {
+                j0 = P.d_idx[d_beg + d_i0];
+                dv0 = P.d_val[d_beg + d_i0];
+            }
+            if (has1) {
+                j1 = P.d_idx[d_beg + d_i0 + D_LANES];
+                dv1 = P.d_val[d_beg + d_i0 + D_LANES];
+            }
+            // the MMAs that last read this stage must be done and its B tile cleared
+            if (chunk >= NSTAGE && !warp_wait(empty0 + 8u * buf, (use - 1u) & 1u, lane, P.status)) {
+                failed = true;
+                break;
+            }
+            // generate A: rows 2 warp, 2 warp + 1; this lane's four voxels
+            const float Xv = (float)(SX + 4 * glx), Yv = (float)(SY + gly), Zv = (float)(SZ + glz);
+            float vals[2][NX_LANE];
 #pragma unroll
-                    for (int rr = 0; rr < 2; ++rr) {
-                        const int r = 2 * warp + rr;
-                        if (r < nrows) {
-                            const float4 A4 = stg[r * 3 + 0];
-                            const float4 B4 = stg[r * 3 + 1];
-                            const float4 C4 = stg[r * 3 + 2];
-                            const float hx = B4.x, hy = B4.y, hz = B4.z;
-                            const float o = fmaf(Xv, hx, fmaf(Yv, hy, Zv * hz));
-                            const float psb = A4.x + o, prb = A4.y + o;
-                            const float c1 = fmaf(Yv, hz, fmaf(-Zv, hy, A4.z));
-                            const float c2 = fmaf(Zv, hx, fmaf(-Xv, hz, A4.w));
-                            const float c3 = fmaf(Xv, hy, fmaf(-Yv, hx, B4.w));
-                            const float c1sq = c1 * c1;
-                            const float c12sq = fmaf(c2, c2, c1sq);
-                            const uint32_t tbf = __float_as_uint(C4.y);
-                            const uint32_t tb = tbf & ~3u;
-                            // warp-uniform choice of the detour form for the whole run of voxels
+            for (int rr = 0; rr < 2; ++rr) {
+                const int r = 2 * warp + rr;
+                if (r < nrows) {
+                    const float4 A4 = stg[r * 3 + 0];
+                    const float4 B4 = stg[r * 3 + 1];
+                    const float4 C4 = stg[r * 3 + 2];
+                    const float hx = B4.x, hy = B4.y, hz = B4.z;
+                    const float o = fmaf(Xv, hx, fmaf(Yv, hy, Zv * hz));
+                    const float psb = A4.x + o, prb = A4.y + o;
+                    const float c1 = fmaf(Yv, hz, fmaf(-Zv, hy, A4.z));
+                    const float c2 = fmaf(Zv, hx, fmaf(-Xv, hz, A4.w));
+                    const float c3 = fmaf(Xv, hy, fmaf(-Yv, hx, B4.w));
+                    const float c1sq = c1 * c1;
+                    const float c12sq = fmaf(c2, c2, c1sq);
+                    const uint32_t tbf = __float_as_uint(C4.y);
+                    const uint32_t tb = tbf & ~3u;
+                    // warp-uniform choice of the detour form for the whole run of voxels
 #define FFT_TC_RUN(INNER_V, PLANAR_V)                                                              \
     _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                        \
         const float ft = (float)t;                                                               \
@@ -314,127 +447,143 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         const float v = detour_v<FFT_DT_STABLE, GUARD, INNER_V>(pst, prt, q2, 0.0f, is, ir);     \
         vals[rr][t] = phi_lookup(v, tb, nm1) * (is * ir) * C4.x;                                 \
     }
-                            if (tbf & 1u) {
-                                if (tbf & 2u) {
-                                    FFT_TC_RUN(true, true)
-                                } else {
-                                    FFT_TC_RUN(true, false)
-                                }
-                            } else {
-                                if (tbf & 2u) {
-                                    FFT_TC_RUN(false, true)
-                                } else {
-                                    FFT_TC_RUN(false, false)
-                                }
-                            }
-#undef FFT_TC_RUN
+                    if (tbf & 1u) {
+                        if (tbf & 2u) {
+                            FFT_TC_RUN(true, true)
                         } else {
-#pragma unroll
-                            for (int t = 0; t < NX_LANE; ++t) vals[rr][t] = 0.0f;
+                            FFT_TC_RUN(true, false)
                         }
-                    }
-#pragma unroll
-                    for (int t = 0; t < NX_LANE; ++t)
-                        *reinterpret_cast<uint32_t*>(sA + tc::kmajor_offset((uint32_t)(32 * t + lane),
-                                                                            (uint32_t)(2 * warp), KC)) =
-                            pack_bf16x2(vals[0][t], vals[1][t]);
-                    // B: clear what this lane wrote into the buffer three chunks ago, then scatter
-                    if (old0 & (1u << 20)) {
-                        for (int j = d_i0; j < P.b_rows; j += D_LANES)
-                            *reinterpret_cast<uint16_t*>(sB + tc::kmajor_offset((uint32_t)j, (uint32_t)d_r, KC)) = 0;
                     } else {
-                        if (old0 & 0x3FFu)
-                            *reinterpret_cast<uint16_t*>(sB + tc::kmajor_offset((old0 & 0x3FFu) - 1u, (uint32_t)d_r, KC)) = 0;
-                        if ((old0 >> 10) & 0x3FFu)
-                            *reinterpret_cast<uint16_t*>(
-                                sB + tc::kmajor_offset(((old0 >> 10) & 0x3FFu) - 1u, (uint32_t)d_r, KC)) = 0;
-                    }
-                    __syncwarp();   // another lane of the half may write where this one cleared
-                    if (has0)
-                        *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j0, (uint32_t)d_r, KC)) =
-                            __float2bfloat16_rn(dv0);
-                    if (has1)
-                        *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j1, (uint32_t)d_r, KC)) =
-                            __float2bfloat16_rn(dv1);
-                    for (int i = d_i0 + 2 * D_LANES; i < d_cnt; i += D_LANES)   // long rows (rare)
-                        *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)P.d_idx[d_beg + i],
-                                                                                 (uint32_t)d_r, KC)) =
-                            __float2bfloat16_rn(P.d_val[d_beg + i]);
-                    const uint32_t now = d_cnt > 2 * D_LANES ? (1u << 20)
-                                                             : (has0 ? j0 + 1u : 0u) | ((has1 ? j1 + 1u : 0u) << 10);
-                    old0 = old1;
-                    old1 = old2;
-                    old2 = now;
-                    // publish this warp's part of the chunk to the MMA warp
-                    tc::fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(full0 + 8u * buf);
-                } else if (lane == 0) {
-                    // MMA warp: wait until all generator warps have written the chunk, then issue
-                    if (!failed && !wait_phase(full0 + 8u * buf, use & 1u)) {
-                        atomicExch(P.status, FFT_ERR_TIMEOUT);
-                        failed = true;
-                    }
-                    tc::fence_after_sync();
-                    const uint32_t a_base = smem_addr(sA), b_base = smem_addr(sB);
-#pragma unroll
-                    for (int ks = 0; ks < KC / 16; ++ks) {
-                        const uint64_t ad = tc::smem_desc(a_base + 256u * ks, 128u, 16u * KC);
-                        for (int h = 0; h < P.nh; ++h) {
-                            const uint64_t bd =
-                                tc::smem_desc(b_base + (uint32_t)(h * P.n_half) * (KC * 2u) + 256u * ks, 128u, 16u * KC);
-                            tc::mma_bf16(taddr + (uint32_t)(h * P.n_half), ad, bd, idesc,
-                                         (unit_chunks > 0 || ks > 0) ? 1u : 0u);
+                        if (tbf & 2u) {
+                            FFT_TC_RUN(false, true)
+                        } else {
+                            FFT_TC_RUN(false, false)
                         }
                     }
-                    tc::mma_commit(empty0 + 8u * buf);
-                }
-                ++chunk;
-                ++unit_chunks;
-                head += nrows;
-            }
-        }
-        if (__syncthreads_or(failed)) break;
-        if (unit_chunks == 0) continue;
-        // ---- 3. all MMAs of this unit done -> TMEM -> Y
-        {
-            const int last = chunk - 1;
-            if (!wait_phase(empty0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1))) {
-                if (tid == 0) atomicExch(P.status, FFT_ERR_TIMEOUT);
-                failed = true;
-            }
-        }
-        if (__syncthreads_or(failed)) break;
-        tc::fence_after_sync();
-        if (is_gen) {
-            const int quarter = warp & 3;              // TMEM lanes this warp may access
-            // TMEM lane 32 quarter + lane holds voxel t = quarter of generation lane `lane`
-            const int x = X0 + 4 * (lane & 1) + quarter, y = Y0 + ((lane >> 1) & 3), z = Z0 + (lane >> 3);
-            const bool valid = x < P.nx && y < P.ny && z < P.nz;
-            const int64_t v = ((int64_t)z * P.ny + y) * P.nx + x;
-            const int cols = P.nh * P.n_half;
-            for (int c = 8 * (warp >> 2); c < cols; c += 32) {
-                float vals[8];
-                tc::tmem_ld_x8(taddr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c, vals);
-                if (valid) {
+#undef FFT_TC_RUN
+                } else {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (c + i < P.n_rhs) P.out[(int64_t)P.col_map[c + i] * P.V + v] = vals[i];
+                    for (int t = 0; t < NX_LANE; ++t) vals[rr][t] = 0.0f;
                 }
             }
+#pragma unroll
+            for (int t = 0; t < NX_LANE; ++t)
+                *reinterpret_cast<uint32_t*>(sA + tc::kmajor_offset((uint32_t)(32 * t + lane), (uint32_t)(2 * warp), KC)) =
+                    pack_bf16x2(vals[0][t], vals[1][t]);
+            // B: the stage was cleared by the MMA warp; scatter this row's D entries
+            if (has0)
+                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j0, (uint32_t)d_r, KC)) = __float2bfloat16_rn(dv0);
+            if (has1)
+                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j1, (uint32_t)d_r, KC)) = __float2bfloat16_rn(dv1);
+            for (int i = d_i0 + 2 * D_LANES; i < d_cnt; i += D_LANES)   // long rows
+                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)P.d_idx[d_beg + i], (uint32_t)d_r, KC)) =
+                    __float2bfloat16_rn(P.d_val[d_beg + i]);
+            // publish this warp's part of the chunk to the MMA warp; release the ring slot
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                tc::mbar_arrive(full0 + 8u * buf);
+                tc::mbar_arrive(ring_empty0 + 8u * slot);
+            }
+            if (h.flags & HDR_LAST) {
+                // ---- all MMAs of the unit done (they complete in order) -> TMEM -> Y
+                if (!warp_wait(done0 + 8u * buf, use & 1u, lane, P.status)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                const int tx = T % P.tiles_x, ty = (T / P.tiles_x) % P.tiles_y, tz = T / (P.tiles_x * P.tiles_y);
+                const int X0 = TILE_X * tx + SX, Y0 = TILE_Y * ty + SY, Z0 = TILE_Z * tz + SZ;
+                const int quarter = warp & 3;   // TMEM lanes this warp may access
+                // TMEM lane 32 quarter + lane holds voxel t = quarter of generation lane `lane`
+                const int x = X0 + 4 * (lane & 1) + quarter, y = Y0 + ((lane >> 1) & 3), z = Z0 + (lane >> 3);
+                const bool valid = x < P.nx && y < P.ny && z < P.nz;
+                const int64_t v = ((int64_t)z * P.ny + y) * P.nx + x;
+                const int cols = P.nh * P.n_half;
+                for (int c = 8 * (warp >> 2); c < cols; c += 32) {
+                    float ov[8];
+                    tc::tmem_ld_x8(taddr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c, ov);
+                    if (valid) {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (c + i < P.n_rhs) P.out[(int64_t)P.col_map[c + i] * P.V + v] = ov[i];
+                    }
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(tmem_free);
+            }
         }
-        tc::fence_before_sync();
-    }
-    // drain: every issued MMA must be complete before the accumulator is released
-    if (chunk > 0) {   // MMAs complete in order: the last one done means all are done
-        const int last = chunk - 1;
-        wait_phase(empty0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1));
+    } else {
+        // ================= MMA warp
+        const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)P.n_half);
+        int units = 0;   // units whose first chunk was issued
+        for (;; ++chunk) {
+            const int slot = chunk % RING;
+            if (!warp_wait(ring_full0 + 8u * slot, (uint32_t)((chunk / RING) & 1), lane, P.status)) {
+                failed = true;
+                break;
+            }
+            const ChunkHdr h = S.hdr[slot];
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(ring_empty0 + 8u * slot);
+            if (h.n_rows < 0) break;
+            const bool first = (h.flags & HDR_FIRST) != 0;
+            // a new accumulation overwrites TMEM: the previous unit's epilogue must have read it
+            if (first && units > 0 && !warp_wait(tmem_free, (uint32_t)((units - 1) & 1), lane, P.status)) {
+                failed = true;
+                break;
+            }
+            if (first) ++units;
+            const int buf = chunk % NSTAGE;
+            const uint32_t use = (uint32_t)(chunk / NSTAGE);
+            if (!warp_wait(full0 + 8u * buf, use & 1u, lane, P.status)) {
+                failed = true;
+                break;
+            }
+            if (lane == 0) {
+                tc::fence_after_sync();
+                const uint32_t a_base = smem_addr(sA0 + buf * a_bytes), b_base = smem_addr(sB0 + buf * b_bytes);
+#pragma unroll
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    const uint64_t ad = tc::smem_desc(a_base + 256u * ks, 128u, 16u * KC);
+                    for (int hh = 0; hh < P.nh; ++hh) {
+                        const uint64_t bd =
+                            tc::smem_desc(b_base + (uint32_t)(hh * P.n_half) * (KC * 2u) + 256u * ks, 128u, 16u * KC);
+                        tc::mma_bf16(taddr + (uint32_t)(hh * P.n_half), ad, bd, idesc, (!first || ks > 0) ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(done0 + 8u * buf);
+            }
+            __syncwarp();
+            // the previous chunk's MMAs are done (they complete in order, before this chunk's):
+            // clear its B tile and hand the stage back to the generators
+            if (chunk > 0) {
+                const int prev = chunk - 1;
+                const int pbuf = prev % NSTAGE;
+                if (!warp_wait(done0 + 8u * pbuf, (uint32_t)((prev / NSTAGE) & 1), lane, P.status)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                uint4* b4 = reinterpret_cast<uint4*>(sB0 + pbuf * b_bytes);
+                for (uint32_t i = lane; i < b_bytes / 16; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
+                tc::fence_proxy_async_smem();
+                tc::mbar_arrive(empty0 + 8u * pbuf);
+            }
+        }
+        // drain: every issued MMA must be complete before the accumulator is released
+        if (chunk > 0) {   // MMAs complete in order: the last one done means all are done
+            const int last = chunk - 1;
+            if (lane == 0) wait_phase(done0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1));
+            __syncwarp();
+        }
+        if (lane == 0 && chunk > 0) atomicAdd(P.chunks, (unsigned long long)chunk);
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(taddr, (uint32_t)P.tmem_cols);
-    if (tid == 0 && chunk > 0) atomicAdd(P.chunks, (unsigned long long)chunk);
 }
 
 }  // namespace
@@ -442,7 +591,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
 static size_t psf_tc_smem(fft_geom g, int b_rows) {
     return NSTAGE * (size_t)(128 * KC * 2) + NSTAGE * (size_t)b_rows * KC * 2 +
            (((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15) +
-           (size_t)LIST_CAP * 3 * sizeof(float4) + sizeof(TcShared) + 1024;
+           (size_t)RING * KC * 3 * sizeof(float4) + sizeof(TcShared) + 1024;
 }
 
 // Largest number of right-hand sides one tensor-core launch can take on this device (the B

@@ -36,6 +36,8 @@ def test_slices32_cg_matches_oracle(slices32):
     d = og.J(wl.model_for(w)) + wl.noise(og.M, w.noise_seed)
     m_ref, hist_ref, rc = og.cgls(d, og.lambda_abs(w.lambda_rel), w.cg_iters)
     assert rc == 0
+    # the damping is relative to |J|_F^2, which each side computes on its own
+    assert geo.frob2() == pytest.approx(og.frob2(), rel=1e-5)
     m, hist = geo.cg_solve(to_dev(d), w.lambda_rel, w.cg_iters, with_history=True)
     err = rel_l2(to_np(m), m_ref)
     print(f"slices32 CG(20) rel-L2 vs oracle {err:.2e}")
@@ -61,5 +63,6 @@ def test_psf_sharp_three_band_all_modes(slices32):
             errs["tc"].append(rel_l2(tc[s, k], ref[s, k]))
     print("PSF rel-L2 vs oracle, max over 18:", {k: f"{max(v):.2e}" for k, v in errs.items()})
     assert max(errs["fp32"]) <= 1e-5
+    assert abs(geo.support_evals - og.count_support()) <= 1e-4 * og.count_support()
     assert max(errs["fp32x4"]) <= 1e-5
     assert max(errs["tc"]) <= 1e-2

@@ -47,6 +47,7 @@ def test_three_band_parity(three_band):
     assert torch.equal(geo.JT(to_dev(d)), JTd)
     assert rel_l2(to_np(geo.coverage()), og.coverage()) <= 1e-5
     assert abs(geo.support_evals - og.count_support()) <= 1e-4 * og.count_support()
+    assert geo.frob2() == pytest.approx(og.frob2(), rel=1e-5)
 
 
 def test_three_band_cg(three_band):
