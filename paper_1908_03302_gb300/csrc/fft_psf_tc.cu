@@ -7,10 +7,12 @@
 // the contraction dimension K and the (subset, spike) columns are N.
 //
 // One persistent CTA per SM runs a pipeline of three warp roles over units (tile, sub-brick):
-//   * 4 scan warps test the tile's candidate rows against the sub-brick (tangent-plane bound
-//     of the convex detour; rows without D entries are dropped), 32 candidates per warp and
-//     block, and append the kept rows' pair-frame records to a ring of 8 chunks of 32 rows in
-//     shared memory, in candidate order (the blocks take turns), so the K order is fixed.
+//   * 4 scan warps stream the tile's compact candidate list (built once per call by
+//     psf_mask_kernel: the tile's candidate rows that have D entries, each with a 16-bit mask
+//     of the sub-bricks its support may reach), keep the rows whose mask holds the unit's
+//     sub-brick, 32 candidates per warp and block, and append the kept rows' pair-frame
+//     records to a ring of 8 chunks of 32 rows in shared memory, in candidate order (the
+//     blocks take turns), so the K order is fixed.
 //     A chunk is published with a header (unit, rows, first / last of the unit) on its
 //     "ring full" mbarrier;
 //   * 16 generator warps take the chunks in order: warp w loads the D entries of rows 2w and
@@ -64,6 +66,10 @@ struct PsfTcParams {
     const int64_t* tile_off;
     const float4* ebase;
     const float* ebase3;
+    int32_t* c_ent;            // compact candidates of each tile (from tile_off[T]): entry id,
+    int32_t* c_row;            //   row,
+    uint16_t* c_mask;          //   sub-bricks the row may reach
+    int32_t* c_cnt;            // compact candidates per tile
     const int32_t* units;      // (tile << 4) | sub-brick, heaviest tiles first
     int n_units;
     int32_t* counter;
@@ -158,6 +164,72 @@ __device__ __forceinline__ void publish_chunk(TcShared& S, uint32_t ring_full0, 
 __device__ __forceinline__ bool ring_slot_free(uint32_t ring_empty0, int chunk, int lane, int32_t* status) {
     if (chunk < RING) return true;
     return warp_wait(ring_empty0 + 8u * (uint32_t)(chunk % RING), (uint32_t)(((chunk / RING) - 1) & 1), lane, status);
+}
+
+constexpr int MASK_THREADS = 256;
+
+// Compact candidate lists, one CTA per tile: the tile's candidate rows that have D entries,
+// each with the mask of its 16 sub-bricks (8 x 4 x 4, inside the grid) that the row's support
+// may reach (tangent-plane bound of the convex detour, as in the J^T kernel), in candidate
+// order, written from tile_off[T]; c_cnt[T] their number and c_or[T] the union of the masks.
+__global__ void __launch_bounds__(MASK_THREADS) psf_mask_kernel(const PsfTcParams P, uint16_t* __restrict__ c_or) {
+    __shared__ int wsum[MASK_THREADS / 32];
+    __shared__ unsigned int s_or;
+    const int T = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tx = T % P.tiles_x, ty = (T / P.tiles_x) % P.tiles_y, tz = T / (P.tiles_x * P.tiles_y);
+    const int64_t e_begin = P.tile_off[T], e_end = P.tile_off[T + 1];
+    if (threadIdx.x == 0) s_or = 0u;
+    __syncthreads();
+    int64_t base = e_begin;
+    unsigned int my_or = 0u;
+    for (int64_t e0 = e_begin; e0 < e_end; e0 += MASK_THREADS) {
+        const int64_t e = e0 + threadIdx.x;
+        unsigned int mask = 0u;
+        int p = 0;
+        if (e < e_end) {
+            p = P.tile_rows[e];
+            if (P.d_off[p + 1] > P.d_off[p]) {   // rows without D entries add nothing
+                const RowRec r = P.rec[p];
+                const BandConst bc = P.bc[P.row_band[p]];
+                const float hb = bc.h;
+                for (int sb = 0; sb < 16; ++sb) {
+                    const int X0 = TILE_X * tx + 8 * (sb & 1), Y0 = TILE_Y * ty + 4 * ((sb >> 1) & 3),
+                              Z0 = TILE_Z * tz + 4 * (sb >> 3);
+                    if (X0 >= P.nx || Y0 >= P.ny || Z0 >= P.nz) continue;
+                    const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
+                    const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
+                    const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
+                    if (box_may_touch(cx, cy, cz, r.b.x, r.b.y, r.b.z, r.a.w, 3.5f * hb, 1.5f * hb, 1.5f * hb))
+                        mask |= 1u << sb;
+                }
+            }
+        }
+        my_or |= mask;
+        const bool keep = mask != 0u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < MASK_THREADS / 32; ++w) {
+            if (w < warp) before += wsum[w];
+            total += wsum[w];
+        }
+        if (keep) {
+            const int64_t pos = base + before + __popc(bal & ((1u << lane) - 1u));
+            P.c_ent[pos] = (int32_t)e;
+            P.c_row[pos] = p;
+            P.c_mask[pos] = (uint16_t)mask;
+        }
+        base += total;
+        __syncthreads();
+    }
+    atomicOr(&s_or, my_or);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        P.c_cnt[T] = (int32_t)(base - e_begin);
+        c_or[T] = (uint16_t)s_or;
+    }
 }
 
 // GUARD: some voxel centre lies on a transducer (the geometry's flag): the guarded detour.
@@ -265,39 +337,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             const int X0 = TILE_X * tx + 8 * (sb & 1), Y0 = TILE_Y * ty + 4 * ((sb >> 1) & 3),
                       Z0 = TILE_Z * tz + 4 * (sb >> 3);
             const bool inside = X0 < P.nx && Y0 < P.ny && Z0 < P.nz;
-            const int64_t e_begin = P.tile_off[T], e_end = P.tile_off[T + 1];
-            const int n_blocks = inside ? (int)((e_end - e_begin + 31) / 32) : 0;
+            const int64_t c_begin = P.tile_off[T];
+            const int n_c = inside ? P.c_cnt[T] : 0;
+            const int n_blocks = (n_c + 31) / 32;
             for (int b = k; b < n_blocks && !failed; b += SCAN_WARPS) {
-                // ---- test this block's 32 candidates (no ordering needed yet)
-                const int64_t e = e_begin + 32 * (int64_t)b + lane;
+                // ---- this block's 32 compact candidates: keep those that reach the sub-brick
+                const int ci = 32 * b + lane;
                 bool keep = false;
                 float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
-                if (e < e_end) {
-                    const int p = P.tile_rows[e];
+                if (ci < n_c && ((P.c_mask[c_begin + ci] >> sb) & 1u)) {
+                    keep = true;
+                    const int64_t e = P.c_ent[c_begin + ci];
+                    const int p = P.c_row[c_begin + ci];
                     const int64_t d0 = P.d_off[p], d1 = P.d_off[p + 1];
-                    if (d1 > d0) {   // rows without D entries add nothing
-                        const RowRec r = P.rec[p];
-                        const int bnd = P.row_band[p];
-                        const BandConst bc = S.bc[bnd];
-                        const float hb = bc.h;
-                        const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
-                        const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
-                        const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
-                        const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
-                        keep = box_may_touch(cx, cy, cz, ex, ey, ez, hl, 3.5f * hb, 1.5f * hb, 1.5f * hb);
-                        if (keep) {
-                            // is the whole sub-brick between the transducer planes? a planar pair?
-                            const float pext = 3.5f * hb * fabsf(ex) + 1.5f * hb * (fabsf(ey) + fabsf(ez)) + 1e-3f;
-                            const bool inner = fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl;
-                            // table base (a multiple of 8) with the inner / planar flags in bits 0, 1
-                            const uint32_t tb = (tab_addr + (uint32_t)(bnd * P.n_tab) * 8u - MAGIC_BITS_X8) |
-                                                (inner ? 1u : 0u) | (ez == 0.0f ? 2u : 0u);
-                            s0 = P.ebase[e];
-                            s1 = make_float4(hb * ex, hb * ey, hb * ez, P.ebase3[e]);
-                            s2 = make_float4(r.b.w, __uint_as_float(tb), __uint_as_float((uint32_t)d0),
-                                             __int_as_float((int)(d1 - d0)));
-                        }
-                    }
+                    const RowRec r = P.rec[p];
+                    const int bnd = P.row_band[p];
+                    const BandConst bc = S.bc[bnd];
+                    const float hb = bc.h;
+                    const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
+                    const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
+                    const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
+                    const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
+                    // is the whole sub-brick between the transducer planes? a planar pair?
+                    const float pext = 3.5f * hb * fabsf(ex) + 1.5f * hb * (fabsf(ey) + fabsf(ez)) + 1e-3f;
+                    const bool inner = fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl;
+                    // table base (a multiple of 8) with the inner / planar flags in bits 0, 1
+                    const uint32_t tb = (tab_addr + (uint32_t)(bnd * P.n_tab) * 8u - MAGIC_BITS_X8) |
+                                        (inner ? 1u : 0u) | (ez == 0.0f ? 2u : 0u);
+                    s0 = P.ebase[e];
+                    s1 = make_float4(hb * ex, hb * ey, hb * ez, P.ebase3[e]);
+                    s2 = make_float4(r.b.w, __uint_as_float(tb), __uint_as_float((uint32_t)d0),
+                                     __int_as_float((int)(d1 - d0)));
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
                 // ---- wait for this block's turn, then append its kept rows in lane order
@@ -625,27 +695,6 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     int cols = nh * n_half, tmem_cols = 32;
     while (tmem_cols < cols) tmem_cols <<= 1;
 
-    // units: the 16 sub-bricks of every tile with candidate rows, heaviest tiles first
-    std::vector<int64_t> toff(g->n_tiles + 1);
-    FFT_CUDA(cudaMemcpy(toff.data(), g->tile_off, sizeof(int64_t) * (g->n_tiles + 1), cudaMemcpyDeviceToHost));
-    std::vector<int32_t> tiles;
-    for (int64_t T = 0; T < g->n_tiles; ++T)
-        if (toff[T + 1] > toff[T]) tiles.push_back((int32_t)T);
-    std::stable_sort(tiles.begin(), tiles.end(),
-                     [&](int32_t a, int32_t b) { return toff[a + 1] - toff[a] > toff[b + 1] - toff[b]; });
-    std::vector<int32_t> units;
-    units.reserve(tiles.size() * 16);
-    for (int32_t T : tiles)
-        for (int s = 0; s < 16; ++s) units.push_back((T << 4) | s);
-    if (units.empty()) return FFT_OK;
-
-    int32_t *d_units = nullptr, *d_ctr = nullptr;
-    FFT_CUDA(cudaMalloc(&d_units, sizeof(int32_t) * units.size()));
-    cudaError_t e = cudaMalloc(&d_ctr, 4 * sizeof(int32_t));   // counter, status, 64-bit chunk count
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_units, units.data(), sizeof(int32_t) * units.size(),
-                                              cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, 4 * sizeof(int32_t), st);
-
     PsfTcParams P;
     P.rec = g->rec;
     P.row_band = g->row_band;
@@ -657,9 +706,6 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     P.tile_off = g->tile_off;
     P.ebase = g->ebase;
     P.ebase3 = g->ebase3;
-    P.units = d_units;
-    P.n_units = (int)units.size();
-    P.counter = d_ctr;
     P.tiles_x = g->tiles[0];
     P.tiles_y = g->tiles[1];
     P.nx = g->grid.nx;
@@ -676,6 +722,65 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     P.tmem_cols = tmem_cols;
     P.out = out;
     P.V = g->V;
+
+    // compact candidate lists (rows with D entries and their sub-brick masks), then the units:
+    // the sub-bricks that some candidate of their tile may reach, heaviest tiles first
+    int32_t *c_ent = nullptr, *c_row = nullptr, *c_cnt = nullptr, *d_units = nullptr, *d_ctr = nullptr;
+    uint16_t *c_mask = nullptr, *c_or = nullptr;
+    auto release = [&]() {
+        cudaFree(c_ent);
+        cudaFree(c_row);
+        cudaFree(c_mask);
+        cudaFree(c_cnt);
+        cudaFree(c_or);
+        cudaFree(d_units);
+        cudaFree(d_ctr);
+    };
+    cudaError_t e = cudaMalloc(&c_ent, sizeof(int32_t) * (size_t)g->E);
+    if (e == cudaSuccess) e = cudaMalloc(&c_row, sizeof(int32_t) * (size_t)g->E);
+    if (e == cudaSuccess) e = cudaMalloc(&c_mask, sizeof(uint16_t) * (size_t)g->E);
+    if (e == cudaSuccess) e = cudaMalloc(&c_cnt, sizeof(int32_t) * (size_t)g->n_tiles);
+    if (e == cudaSuccess) e = cudaMalloc(&c_or, sizeof(uint16_t) * (size_t)g->n_tiles);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ctr, 4 * sizeof(int32_t));   // counter, status, 64-bit chunk count
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "psf tensor-core path: candidate lists");
+    }
+    P.c_ent = c_ent;
+    P.c_row = c_row;
+    P.c_mask = c_mask;
+    P.c_cnt = c_cnt;
+    psf_mask_kernel<<<(unsigned)g->n_tiles, MASK_THREADS, 0, st>>>(P, c_or);
+    e = cudaGetLastError();
+    std::vector<int32_t> cnt(g->n_tiles);
+    std::vector<uint16_t> ors(g->n_tiles);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), c_cnt, sizeof(int32_t) * cnt.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ors.data(), c_or, sizeof(uint16_t) * ors.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "psf tensor-core path: candidate lists");
+    }
+    std::vector<int32_t> tiles;
+    for (int64_t T = 0; T < g->n_tiles; ++T)
+        if (cnt[T] > 0) tiles.push_back((int32_t)T);
+    std::stable_sort(tiles.begin(), tiles.end(), [&](int32_t a, int32_t b) { return cnt[a] > cnt[b]; });
+    std::vector<int32_t> units;
+    units.reserve(tiles.size() * 16);
+    for (int32_t T : tiles)
+        for (int s = 0; s < 16; ++s)
+            if ((ors[T] >> s) & 1u) units.push_back((T << 4) | s);
+    if (units.empty()) {
+        release();
+        return FFT_OK;
+    }
+    e = cudaMalloc(&d_units, sizeof(int32_t) * units.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_units, units.data(), sizeof(int32_t) * units.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ctr, 0, 4 * sizeof(int32_t), st);
+    P.units = d_units;
+    P.n_units = (int)units.size();
+    P.counter = d_ctr;
     P.status = d_ctr + 1;
     P.chunks = reinterpret_cast<unsigned long long*>(d_ctr + 2);
 
@@ -686,8 +791,7 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess && smem + sizeof(TcShared) > (size_t)optin) {
-        cudaFree(d_units);
-        cudaFree(d_ctr);
+        release();
         set_error("psf tensor-core path: tables and tiles do not fit in shared memory");
         return FFT_ERR_ARG;
     }
@@ -709,8 +813,7 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     memcpy(&nch, hs + 2, sizeof(nch));
     // MMA work of this launch: every chunk multiplies a 128 x 32 BF16 tile by 32 x cols
     g->psf_tc_mma_flops += 2.0 * 128.0 * KC * (double)cols * (double)nch;
-    cudaFree(d_units);
-    cudaFree(d_ctr);
+    release();
     if (e != cudaSuccess) return cuda_fail(e, "psf tensor-core path");
     if (status != 0) {
         set_error("psf tensor-core path: a bounded wait for the tensor cores timed out");
