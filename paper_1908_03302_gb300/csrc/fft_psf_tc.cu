@@ -7,26 +7,31 @@
 // the contraction dimension K and the (subset, spike) columns are N.
 //
 // One persistent CTA per SM runs a pipeline of three warp roles over units (tile, sub-brick):
-//   * 4 scan warps stream the tile's compact candidate list (built once per call by
+//   * 2 scan warps stream the tile's compact candidate list (built once per call by
 //     psf_mask_kernel: the tile's candidate rows that have D entries, each with a 16-bit mask
 //     of the sub-bricks its support may reach), keep the rows whose mask holds the unit's
 //     sub-brick, 32 candidates per warp and block, and append the kept rows' pair-frame
-//     records to a ring of 8 chunks of 32 rows in shared memory, in candidate order (the
+//     records to a ring of 8 chunks of 48 rows in shared memory, in candidate order (the
 //     blocks take turns), so the K order is fixed.
 //     A chunk is published with a header (unit, rows, first / last of the unit) on its
 //     "ring full" mbarrier;
-//   * 16 generator warps take the chunks in order: warp w loads the D entries of rows 2w and
+//   * 24 generator warps take the chunks in order: warp w loads the D entries of rows 2w and
 //     2w + 1, generates those two rows of the A tile J[p, v] (FP32 evaluation as in the J^T
 //     kernel, rounded to BF16), scatters the rows' D entries (BF16) into the chunk's B tile and
 //     arrives on the stage's "full" mbarrier; after the last chunk of a unit they move the
 //     accumulator TMEM -> registers -> Y and arrive on "TMEM free";
-//   * 1 MMA warp waits for "full", issues tcgen05.mma (M = 128, N = up to 2 x 256, K = 32;
+//   * 1 MMA warp waits for "full", issues tcgen05.mma (M = 128, N = up to 2 x 256, K = 48;
 //     the unit's first chunk starts a new accumulation, after "TMEM free") and commits to the
 //     stage's "done" mbarrier; one chunk later it waits for those MMAs, clears the stage's B
 //     tile (dense 16-byte stores) and arrives on "empty", which the generators wait for before
 //     reusing the stage.
 // Three A / B stages and the 8-chunk row ring decouple the roles: no CTA-wide barrier between
-// the first and the last unit. Every wait is bounded; a thread whose wait timed out sets a
+// the first and the last unit. Six generator warps per SM sub-partition hide the latency of
+// the evaluation chains (four left the issue slots a third idle). The Phi tables are held in
+// shared memory; where the geometry's tables and the stages do not fit together, the kernel
+// takes the tables at half resolution (resampled from the device tables by the linear
+// interpolant; the extra interpolation error, ~2e-5 of max |Phi|, is far below the BF16
+// rounding of the entries). Every wait is bounded; a thread whose wait timed out sets a
 // status word and leaves its loop, so that the others time out in turn and the CTA ends.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -44,12 +49,12 @@ namespace fftgb {
 
 namespace {
 
-constexpr int GEN_WARPS = 16;          // warps that generate J and scatter D (warps 0 .. 15)
-constexpr int SCAN_WARPS = 4;          // warps that scan candidate rows (warps 16 .. 19)
+constexpr int GEN_WARPS = 24;          // warps that generate J and scatter D (warps 0 .. 23)
+constexpr int SCAN_WARPS = 2;          // warps that scan candidate rows (warps 24, 25)
 constexpr int MMA_WARP = GEN_WARPS + SCAN_WARPS;   // the warp that issues the MMAs
 constexpr int TC_WARPS = MMA_WARP + 1;
 constexpr int TC_THREADS = TC_WARPS * 32;
-constexpr int KC = 32;                 // rows per chunk (MMA K per chunk): 2 per generator warp
+constexpr int KC = 2 * GEN_WARPS;      // rows per chunk (MMA K per chunk): 2 per generator warp
 constexpr int NSTAGE = 3;              // A / B stages
 constexpr int RING = 8;                // chunks of staged rows between the scan and the generation
 constexpr int D_LANES = 16;            // lanes that scatter one row's D entries
@@ -570,7 +575,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                 const bool valid = x < P.nx && y < P.ny && z < P.nz;
                 const int64_t v = ((int64_t)z * P.ny + y) * P.nx + x;
                 const int cols = P.nh * P.n_half;
-                for (int c = 8 * (warp >> 2); c < cols; c += 32) {
+                for (int c = 8 * (warp >> 2); c < cols; c += 8 * (GEN_WARPS / 4)) {
                     float ov[8];
                     tc::tmem_ld_x8(taddr + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c, ov);
                     if (valid) {
@@ -658,10 +663,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
 
 }  // namespace
 
-static size_t psf_tc_smem(fft_geom g, int b_rows) {
+static size_t psf_tc_smem(fft_geom g, int b_rows, int n_tab) {
     return NSTAGE * (size_t)(128 * KC * 2) + NSTAGE * (size_t)b_rows * KC * 2 +
-           (((size_t)g->n_bands * g->n_tab * sizeof(float2) + 15) & ~(size_t)15) +
+           (((size_t)g->n_bands * n_tab * sizeof(float2) + 15) & ~(size_t)15) +
            (size_t)RING * KC * 3 * sizeof(float4) + sizeof(TcShared) + 1024;
+}
+
+// Table length the tensor-core kernel uses: the geometry's, or half of it (n -> (n + 1) / 2
+// samples) while all band tables take more than 48 KB of shared memory.
+static int psf_tc_table_len(fft_geom g) {
+    int n = g->n_tab;
+    while (n > 64 && (size_t)g->n_bands * n * sizeof(float2) > 48 * 1024) n = (n + 1) / 2;
+    return n;
+}
+
+// Band tables at n2 samples from the device tables at n samples (packed as (Phi_k - k dPhi_k,
+// (n - 1) dPhi_k)): Phi at v = k / (n2 - 1) by the linear interpolant of the original, in FP64,
+// packed the same way; the last entry is the cut-off (0, 0).
+__global__ void psf_tc_resample_kernel(const float2* __restrict__ tab, int n, int n_bands, int n2,
+                                       float2* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_bands * n2) return;
+    const int b = i / n2, k = i % n2;
+    const float2* t = tab + (size_t)b * n;
+    auto phi = [&](int kk) -> double {
+        if (kk >= n2 - 1) return 0.0;
+        const double v = (double)kk / (double)(n2 - 1);
+        int j = (int)floor(v * (double)(n - 1));
+        j = j < 0 ? 0 : (j > n - 2 ? n - 2 : j);
+        return (double)t[j].x + v * (double)t[j].y;
+    };
+    if (k == n2 - 1) {
+        out[i] = make_float2(0.0f, 0.0f);
+    } else {
+        const double p0 = phi(k), d = phi(k + 1) - p0;
+        out[i] = make_float2((float)(p0 - (double)k * d), (float)(d * (double)(n2 - 1)));
+    }
 }
 
 // Largest number of right-hand sides one tensor-core launch can take on this device (the B
@@ -674,7 +711,7 @@ int psf_tc_max_cols(fft_geom g) {
     for (int c = 16; c <= 512; c += 16) {
         const int nh = c > 256 ? 2 : 1;
         const int n_half = (int)ceil_div(ceil_div(c, nh), 16) * 16;
-        if (psf_tc_smem(g, nh * n_half) <= (size_t)optin) best = c;
+        if (psf_tc_smem(g, nh * n_half, psf_tc_table_len(g)) <= (size_t)optin) best = c;
     }
     return best;
 }
@@ -702,6 +739,7 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     P.tab = g->tab;
     P.n_bands = g->n_bands;
     P.n_tab = g->n_tab;
+    const int n_tab_tc = psf_tc_table_len(g);
     P.tile_rows = g->tile_rows;
     P.tile_off = g->tile_off;
     P.ebase = g->ebase;
@@ -727,7 +765,9 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     // the sub-bricks that some candidate of their tile may reach, heaviest tiles first
     int32_t *c_ent = nullptr, *c_row = nullptr, *c_cnt = nullptr, *d_units = nullptr, *d_ctr = nullptr;
     uint16_t *c_mask = nullptr, *c_or = nullptr;
+    float2* tab_tc = nullptr;
     auto release = [&]() {
+        cudaFree(tab_tc);
         cudaFree(c_ent);
         cudaFree(c_row);
         cudaFree(c_mask);
@@ -742,6 +782,15 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     if (e == cudaSuccess) e = cudaMalloc(&c_cnt, sizeof(int32_t) * (size_t)g->n_tiles);
     if (e == cudaSuccess) e = cudaMalloc(&c_or, sizeof(uint16_t) * (size_t)g->n_tiles);
     if (e == cudaSuccess) e = cudaMalloc(&d_ctr, 4 * sizeof(int32_t));   // counter, status, 64-bit chunk count
+    if (e == cudaSuccess && n_tab_tc != g->n_tab) {
+        e = cudaMalloc(&tab_tc, sizeof(float2) * (size_t)g->n_bands * n_tab_tc);
+        if (e == cudaSuccess) {
+            const int nt = g->n_bands * n_tab_tc;
+            psf_tc_resample_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, st>>>(g->tab, g->n_tab, g->n_bands,
+                                                                                n_tab_tc, tab_tc);
+            e = cudaGetLastError();
+        }
+    }
     if (e != cudaSuccess) {
         release();
         return cuda_fail(e, "psf tensor-core path: candidate lists");
@@ -784,8 +833,12 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     P.status = d_ctr + 1;
     P.chunks = reinterpret_cast<unsigned long long*>(d_ctr + 2);
 
+    if (tab_tc) {   // the kernel's tables: the resampled ones
+        P.tab = tab_tc;
+        P.n_tab = n_tab_tc;
+    }
     // at least 120 KB so that only one CTA (which holds TMEM for the whole launch) fits on an SM
-    const size_t smem = std::max<size_t>(120 * 1024, psf_tc_smem(g, P.b_rows) - sizeof(TcShared) - 1024);
+    const size_t smem = std::max<size_t>(120 * 1024, psf_tc_smem(g, P.b_rows, n_tab_tc) - sizeof(TcShared) - 1024);
     int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
