@@ -1,10 +1,14 @@
-"""Parity at the full size of the single-ring workload the benchmark times (256 elements on a
-100 mm ring, 32640 pairs, 200 x 200 x 40 voxels at 1 mm, nested-cylinder model): J on
-sampled rows and J^T on sampled voxels against the FP64 oracle (which computes those
-outputs one by one), and properties of the 30-iteration CG that hold at any size: the
-normal-equations residual it reports falls, the solution reduces the damped misfit
-(CGLS minimises it over growing Krylov spaces), the graph replay is bit-reproducible and
-the reconstruction correlates with the true model."""
+"""Parity at the full size of the single-ring workload (256 elements on a 100 mm ring, 32640
+pairs, 200 x 200 x 40 voxels at 1 mm, nested-cylinder model): J on sampled rows and J^T on
+sampled voxels against the FP64 oracle (which computes those outputs one by one); the
+30-iteration damped CGLS solve against the oracle's own solve of the same data, stored in
+tests/golden/ring256_cgls30.npz by tests/golden/make_ring256_cgls.py (the oracle needs over
+an hour for it); and properties of the solve that hold at any size: the normal-equations
+residual it reports falls, the solution reduces the damped misfit (CGLS minimises it over
+growing Krylov spaces), the graph replay is bit-reproducible and the reconstruction
+correlates with the true model."""
+import os
+
 import numpy as np
 import pytest
 
@@ -62,3 +66,16 @@ def test_ring256_cg_properties(ring256):
     assert torch.equal(m, m2)
     c = float(torch.nn.functional.cosine_similarity(m.double(), m_true.double(), dim=0))
     assert c > 0.3
+
+
+def test_ring256_cg_matches_stored_oracle_solve(ring256):
+    # Sec. II-D, Eq. leastSquare_misfit: 30 CGLS iterations from m0 = 0 with relative damping
+    # 1e-3; relative L2 <= 1e-4 on the model, as for the smaller solves
+    w, og, geo = ring256
+    ref = np.load(os.path.join(os.path.dirname(__file__), "golden", "ring256_cgls30.npz"))
+    assert geo.frob2() == pytest.approx(float(ref["frob2"]), rel=1e-5)
+    m, hist = geo.cg_solve(to_dev(ref["d"]), w.lambda_rel, w.cg_iters, with_history=True)
+    err = rel_l2(to_np(m), ref["m"].astype(np.float64))
+    print(f"ring256 CG(30) rel-L2 vs the stored FP64 oracle solve {err:.2e}")
+    assert err <= 1e-4
+    assert np.allclose(hist, ref["hist"], rtol=1e-3)
