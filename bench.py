@@ -51,7 +51,9 @@ FP32_LANES_PER_SM_CLK = 128
 # workload, from ncu captures of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum); a workload without a capture of the current build reports null.
 APPLY_TRAFFIC_BYTES = {
-    "ring256": 349740800,   # apply 87283456 + 109496576, jt_reduce 151964672 + 996096
+    # plain-band apply 4025283072 + 151932160, sharp-band apply 5192666624 + 385817856,
+    # jt_reduce 342402304 + 6704640
+    "slices3d": 10104806656,
 }
 
 
