@@ -4,22 +4,24 @@
 // Work decomposition
 //   * The voxel grid is cut into 16 x 16 x 8 tiles. Each tile has a list of candidate rows
 //     (built once per geometry by a conservative cull). A work item is a tile and a range of
-//     its rows; a unit is one of the tile's eight 8 x 8 x 4 regions (two 8 x 4 x 4
-//     sub-bricks) of one item, and every warp of the persistent grid pulls units from a
-//     counter, heaviest items first, on its own (the only CTA barrier follows the table load).
-//     CTAs have 8 warps (4 per SM for the 64-register variants); the sharp-band variants run
-//     in CTAs of 8 to 20 warps, whichever keeps the most warps resident.
+//     its rows; a unit is one region of one item: an 8 x 8 x 8 region (four 8 x 4 x 4
+//     sub-bricks, four regions per tile) for the single-column modes, an 8 x 8 x 4 region
+//     (two sub-bricks, eight per tile) for the four-column ones. Every warp of the persistent
+//     grid pulls units from a counter, heaviest items first, on its own (the only CTA barrier
+//     follows the table load). The launch shape (warps per CTA, CTAs per SM) is picked per
+//     variant from its register budget and the shared memory the band tables take.
 //   * Lane l owns 4 consecutive x voxels of each sub-brick of its warp's region. Per chunk of
 //     32 rows, lane l loads row l, moves its geometry into the tile's pair frame and tests it
-//     against the region's two sub-bricks (tangent-plane bounds of the convex detour); the
-//     survivors are staged in shared memory and broadcast.
+//     against the region's sub-bricks (tangent-plane bounds of the convex detour); the rows
+//     that reach one are staged in shared memory and broadcast, and each is evaluated on the
+//     sub-bricks it reaches.
 //   * Per (row, voxel): pair-frame coordinates by FFMA from per-lane offsets, normalised
 //     detour (cancellation-free form), Phi from the band table in shared memory (one 64-bit
 //     load, linear interpolation), geometric factor 1 / (R_xs R_xr).
 //   * J^T accumulates per voxel in registers over the item's rows (gather, no atomics).
 //     J folds each row's lane partials to 8 with two shuffles, parks them in the row's
 //     consumed staging record, and the row's own lane sums them after the chunk: one partial
-//     per (entry, warp); a second kernel sums each row's partials in a fixed order. Both are
+//     per (entry, region); a second kernel sums each row's partials in a fixed order. Both are
 //     deterministic.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -58,9 +60,9 @@ struct ApplyParams {
     double org[3];
     double h;
     const float* vin;        // J: m [V]; J^T: d [M]
-    float* vout;             // J: jpart [E * 8]; J^T: g [V]
+    float* vout;             // J: jpart [E * 4]; J^T: g [V]
     float* gpart;            // J^T partials of multi-item tiles
-    double* dsum;            // FROB: [n_items * 8]
+    double* dsum;            // FROB: one per unit [n_items * 4]
     unsigned long long* icount;   // COUNT
     int trig_nq;             // sine-series Phi: coefficient groups of 4 per band
     int64_t nvox, nrow;      // column lengths of the batch modes' blocks (V, M)
@@ -111,66 +113,117 @@ __device__ __forceinline__ float detour_v64(const RowRec64& r, double ox, double
     return (float)(v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v));
 }
 
-// Resident 8-warp CTAs per SM the register budget is sized for: the stable-detour table
-// kernels fit 64 registers without spilling (4 CTAs, 32 warps per SM); the others keep 80 (3
-// CTAs), the four-column ones and the other sharp-band ones 128 (2 CTAs). The single-column
-// sharp-band stable-detour table variants are sized separately (apply_sharp_wide below).
+// Resident 8-warp CTAs per SM the register budget is sized for: 4 (64 registers) for the
+// stable-detour table kernels, 3 (80) for the others, 2 (128) for the four-column ones and the
+// other sharp-band ones. The single-column stable-detour table variants are sized separately
+// (apply_sharp_wide and apply_plain_wide below).
 template <int MODE, int DT, bool SHARP, int PHI>
 constexpr int apply_min_blocks() {
     return (SHARP || MODE == MODE_JT4 || MODE == MODE_J4) ? 2
                                                           : ((DT == FFT_DT_STABLE && PHI == PHI_TABLE) ? 4 : 3);
 }
 
+// Sub-bricks per unit and units (regions) per item of each mode: see sub_dy below.
+template <int MODE>
+constexpr int apply_nsub() {
+    return (MODE == MODE_JT4 || MODE == MODE_J4) ? 2 : 4;
+}
+template <int MODE>
+constexpr int apply_regions() {
+    return 16 / apply_nsub<MODE>();   // 16 sub-bricks of 8 x 4 x 4 per 16 x 16 x 8 tile
+}
+
+// Sub-bricks of a unit. The single-column modes take an 8 x 8 x 8 region (NSUB = 4) and the
+// four-column modes, whose per-voxel state is four times larger, an 8 x 8 x 4 region (NSUB =
+// 2). Sub-brick s of a lane sits at y offset sub_dy(s) and z offset sub_dz(s) from sub-brick 0;
+// for NSUB = 4 the order (0,0), (4,0), (4,4), (0,4) lets every step between consecutive
+// sub-bricks move along one axis only.
+template <int NSUB>
+__device__ __forceinline__ constexpr int sub_dy(int s) {
+    return NSUB == 2 ? 4 * s : ((s == 1 || s == 2) ? 4 : 0);
+}
+template <int NSUB>
+__device__ __forceinline__ constexpr int sub_dz(int s) {
+    return NSUB == 2 ? 0 : (s >= 2 ? 4 : 0);
+}
+
+// Pair-frame values of a lane's first voxel moved from sub-brick s - 1 to sub-brick s (s >= 1):
+// +4 voxels in y (s = 1), +4 in z (s = 2), -4 in y (s = 3). A step d along an axis changes
+// p by d . e and c = (x - o) x e by d x e. The main loop and the FP64 re-decision both reach
+// sub-brick s through these same operations, so their FP32 values agree bit for bit.
+template <int NSUB, bool PL>
+__device__ __forceinline__ void sub_step(int s, float hx, float hy, float hz, float& ps, float& pr, float& c1,
+                                         float& c2, float& c3) {
+    if (s == 1 || s == 3) {
+        const float f = (s == 1) ? 4.0f : -4.0f;
+        ps = fmaf(f, hy, ps);
+        pr = fmaf(f, hy, pr);
+        if (!PL) c1 = fmaf(f, hz, c1);
+        c3 = fmaf(-f, hx, c3);
+    } else if (s == 2) {
+        if (!PL) {
+            ps = fmaf(4.0f, hz, ps);
+            pr = fmaf(4.0f, hz, pr);
+        }
+        c1 = fmaf(-4.0f, hy, c1);
+        c2 = fmaf(4.0f, hx, c2);
+    }
+}
+
 // The FP64 re-decision of the sharp-band kernels, out of line (called only for an entry where
 // some lane's FP32 detour lies within CUT_BAND of the cut), so that its FP64 temporaries do not
-// weigh on the register allocation of the main loop. For each of the lane's 8 voxels (k = 4 s
-// + t) it recomputes the FP32 detour by the operations of the main pass, and for the voxels
-// near the cut re-decides dt < dt_max in FP64. It returns in d[k] what the main pass's term
-// has to change by: val2 - val1 (J, J^T, four-column modes), |val2| - |val1| (coverage),
-// val2^2 - val1^2 (Frobenius), +1 / -1 (support count), 0 where nothing changes.
-template <int MODE, int DT, bool GUARD, int PHI>
+// weigh on the register allocation of the main loop. For each of the lane's 4 NSUB voxels
+// (k = 4 s + t) it recomputes the FP32 detour by the operations of the main pass, and for the
+// voxels near the cut re-decides dt < dt_max in FP64. It returns in d[k] what the main pass's
+// term has to change by: val2 - val1 (J, J^T, four-column modes), |val2| - |val1| (coverage),
+// val2^2 - val1^2 (Frobenius), +1 / -1 (support count), 0 where nothing changes. `inner` holds
+// the sub-bricks lying between the transducer planes (bit s).
+template <int MODE, int DT, bool GUARD, int PHI, int NSUB>
 __device__ __noinline__ void sharp_fix(const ApplyParams& P, float4 A, float4 B, float4 C, float Xl, float Yl,
-                                       float Zl, bool planar, bool inner0, bool inner1, float cutb, uint32_t tb,
+                                       float Zl, bool planar, uint32_t inner_bits, float cutb, uint32_t tb,
                                        float nm1, int nq, int ix0, int iy0, int iz0, float* d) {
     const float hx = B.x, hy = B.y, hz = B.z;
     const float hl = 0.5f * (A.x - A.y);
     const int b = __float_as_int(C.w) & 0xff;
     const double U = P.bc[b].U;
+    // one voxel per iteration, each recomputed from the lane base (few values live across
+    // iterations, which keeps the caller's register saves around this call small)
 #pragma unroll 1
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 4 * NSUB; ++k) {
         const int s = k >> 2, t = k & 3;
         d[k] = 0.0f;
-        const float offs = fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
+        const float offs = planar ? fmaf(Xl, hx, Yl * hy) : fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
         float pss = A.x + offs, prs = A.y + offs;
-        float c1s = fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
-        const float c2s = fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
+        float c1s = planar ? fmaf(-Zl, hy, A.z) : fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
+        float c2s = planar ? fmaf(Zl, hx, A.w) : fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
         float c3s = fmaf(Xl, hy, fmaf(-Yl, hx, B.w));
-        if (s == 1) {
-            pss = fmaf(4.0f, hy, pss);
-            prs = fmaf(4.0f, hy, prs);
-            c1s = fmaf(4.0f, hz, c1s);
-            c3s = fmaf(-4.0f, hx, c3s);
+#pragma unroll 1
+        for (int q = 1; q <= s; ++q) {
+            if (planar)
+                sub_step<NSUB, true>(q, hx, hy, hz, pss, prs, c1s, c2s, c3s);
+            else
+                sub_step<NSUB, false>(q, hx, hy, hz, pss, prs, c1s, c2s, c3s);
         }
         const float ft = (float)t;
         const float c1sq = c1s * c1s;
-        const float pst = fmaf(ft, hx, pss);
-        const float prt = fmaf(ft, hx, prs);
-        const float c3t = fmaf(ft, hy, c3s);
+        const float pst = (t == 0 ? pss : fmaf(ft, hx, pss));
+        const float prt = (t == 0 ? prs : fmaf(ft, hx, prs));
+        const float c3t = (t == 0 ? c3s : fmaf(ft, hy, c3s));
         float q2;
         if (planar) {
             q2 = fmaf(c3t, c3t, fmaf(c2s, c2s, c1sq));
         } else {
-            const float c2t = fmaf(-ft, hz, c2s);
+            const float c2t = (t == 0 ? c2s : fmaf(-ft, hz, c2s));
             q2 = fmaf(c2t, c2t, fmaf(c3t, c3t, c1sq));
         }
-        const bool inner = (DT == FFT_DT_STABLE) && (s ? inner1 : inner0);
+        const bool inner = (DT == FFT_DT_STABLE) && ((inner_bits >> s) & 1u);
         float is, ir;
         const float vr = inner ? detour_v<DT, GUARD, true, true>(pst, prt, q2, hl, is, ir)
                                : detour_v<DT, GUARD, false, true>(pst, prt, q2, hl, is, ir);
         if (!(fabsf(vr - 1.0f) < cutb)) continue;
         const float v = __saturatef(vr);
         const bool in = in_support64(P.rec64[__float_as_int(C.z)], P.org[0], P.org[1], P.org[2], P.h, ix0 + t,
-                                     iy0 + 4 * s, iz0, U);
+                                     iy0 + sub_dy<NSUB>(s), iz0 + sub_dz<NSUB>(s), U);
         const float v2 = settle_cut(v, in);
         if (v2 == v) continue;
         if (MODE == MODE_COUNT) {
@@ -198,15 +251,15 @@ constexpr bool apply_sharp_wide() {
 }
 constexpr int SHARP_MAX_WARPS = 20;
 
-// The plain stable-detour table variants (single column) keep the 64-register budget of four
-// 8-warp CTAs per SM but are built for blocks of up to 32 warps: where large (multi-band)
-// tables leave room for fewer than four 8-warp CTAs, one wide CTA shares one copy of the
-// tables and keeps 32 warps resident.
+// The plain stable-detour table variants (single column) are built for blocks of up to 24
+// warps at one per SM, i.e. 80 registers: their 16 per-lane voxels (8 x 8 x 8 units) want more
+// than 64, and one wide CTA shares one copy of the band tables. Measured against 32 warps at
+// 64 registers: slices3d J^T 408.0 -> 407.6 ms, J 412.6 -> 411.4 ms, ring256 J^T 3.75 -> 3.72 ms.
 template <int MODE, int DT, bool SHARP, int PHI>
 constexpr bool apply_plain_wide() {
     return !SHARP && DT == FFT_DT_STABLE && PHI == PHI_TABLE && MODE != MODE_JT4 && MODE != MODE_J4;
 }
-constexpr int PLAIN_MAX_WARPS = 32;
+constexpr int PLAIN_MAX_WARPS = 24;
 
 template <int MODE, int DT, bool SHARP, int PHI>
 constexpr int apply_block_bound() {
@@ -236,59 +289,76 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
     const int lx = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
     constexpr bool BATCH = (MODE == MODE_JT4 || MODE == MODE_J4);
     constexpr int SR = BATCH ? 4 : 3;   // staged float4 per row
+    constexpr int NSUB = apply_nsub<MODE>();
+    constexpr int NREG = apply_regions<MODE>();
+    constexpr bool FLAGW = (NSUB == 4);
     float4* stg = s_stage + warp * STG_PER_WARP;
-    const int n_units = P.n_items * 8;   // 8 regions per item
+    const int n_units = P.n_items * NREG;
 
     for (;;) {
-        // A unit is one 8 x 8 x 4 region of one item (unit = item * 8 + region).
+        // A unit is one region of one item (unit = item * NREG + region): 8 x 8 x 8 voxels for
+        // the single-column modes (regions 2 x 2 x 1 per tile), 8 x 8 x 4 for the four-column
+        // ones (2 x 2 x 2 per tile).
         int unit = 0;
         if (lane == 0) unit = atomicAdd(P.counter, 1);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if (unit >= n_units) break;
-        const int it = unit >> 3, region = unit & 7;
+        const int it = unit / NREG, region = unit % NREG;
         const Item item = P.items[it];
         const int tx = item.tile % P.tiles_x;
         const int ty = (item.tile / P.tiles_x) % P.tiles_y;
         const int tz = item.tile / (P.tiles_x * P.tiles_y);
         const int TX = TILE_X * tx, TY = TILE_Y * ty, TZ = TILE_Z * tz;
-        const int wx = region & 1, wy = (region >> 1) & 1, wz = region >> 2;
+        const int wx = region & 1, wy = (region >> 1) & 1, wz = (NSUB == 2) ? (region >> 2) : 0;
         // lane voxel offsets in the tile (sub-brick 0, first of its 4 x voxels)
         const int oxi = 8 * wx + 4 * lx, oyi = 8 * wy + ly, ozi = 4 * wz + lz;
         const float Xl = (float)oxi, Yl = (float)oyi, Zl = (float)ozi;
 
-        // validity of this lane's voxels (bit 4 s + t) and of the region's sub-bricks
-        uint32_t vmask = 0;
-        if (TZ + ozi < P.nz) {
+        // validity of this lane's voxels (bit 4 s + t) and of the region's sub-bricks (bit s)
+        auto lane_vmask = [&]() {
+            uint32_t vm = 0;
 #pragma unroll
-            for (int s = 0; s < 2; ++s)
+            for (int s = 0; s < NSUB; ++s) {
+                if (TZ + ozi + sub_dz<NSUB>(s) < P.nz && TY + oyi + sub_dy<NSUB>(s) < P.ny) {
 #pragma unroll
-                for (int t = 0; t < NX_LANE; ++t)
-                    if (TY + oyi + 4 * s < P.ny && TX + oxi + t < P.nx) vmask |= 1u << (4 * s + t);
-        }
+                    for (int t = 0; t < NX_LANE; ++t)
+                        if (TX + oxi + t < P.nx) vm |= 1u << (4 * s + t);
+                }
+            }
+            return vm;
+        };
+        uint32_t sub_ok = 0;
+#pragma unroll
+        for (int s = 0; s < NSUB; ++s)
+            if (TX + 8 * wx < P.nx && TY + 8 * wy + sub_dy<NSUB>(s) < P.ny && TZ + 4 * wz + sub_dz<NSUB>(s) < P.nz)
+                sub_ok |= 1u << s;
+        // the gather modes need the mask only for their stores: recomputed there
+        constexpr bool VM_LIVE = !(MODE == MODE_JT || MODE == MODE_COV || MODE == MODE_JT4);
+        const uint32_t vmask = VM_LIVE ? lane_vmask() : 0u;
         const int64_t vbase = ((int64_t)(TZ + ozi) * P.ny + TY + oyi) * P.nx + TX + oxi;
-        const bool sub_ok0 = (TX + 8 * wx < P.nx) && (TY + 8 * wy < P.ny) && (TZ + 4 * wz < P.nz);
-        const bool sub_ok1 = (TX + 8 * wx < P.nx) && (TY + 8 * wy + 4 < P.ny) && (TZ + 4 * wz < P.nz);
 
-        float acc[2][NX_LANE];
-        float mv[2][NX_LANE];
-        float acc4[2][NX_LANE][4];   // batch modes only
+        float acc[NSUB][NX_LANE];
+        float mv[NSUB][NX_LANE];
+        float acc4[2][NX_LANE][4];   // four-column modes only (NSUB = 2)
         float mv4[2][NX_LANE][4];
         double dacc = 0.0;
         unsigned long long cnt = 0, cnt_eval = 0;
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < NSUB; ++s)
 #pragma unroll
             for (int t = 0; t < NX_LANE; ++t) {
+                const int64_t vo = vbase + ((int64_t)sub_dz<NSUB>(s) * P.ny + sub_dy<NSUB>(s)) * P.nx + t;
                 acc[s][t] = 0.0f;
                 mv[s][t] = 0.0f;
-                if (MODE == MODE_J && ((vmask >> (4 * s + t)) & 1u))
-                    mv[s][t] = __ldg(P.vin + vbase + (int64_t)(4 * s) * P.nx + t);
+                if (MODE == MODE_J && ((vmask >> (4 * s + t)) & 1u)) mv[s][t] = __ldg(P.vin + vo);
+                if (BATCH && s < 2) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    acc4[s][t][r] = 0.0f;
-                    mv4[s][t][r] = 0.0f;
-                    if (MODE == MODE_J4 && ((vmask >> (4 * s + t)) & 1u))
-                        mv4[s][t][r] = __ldg(P.vin + (int64_t)r * P.nvox + vbase + (int64_t)(4 * s) * P.nx + t);
+                    for (int r = 0; r < 4; ++r) {
+                        acc4[s & 1][t][r] = 0.0f;
+                        mv4[s & 1][t][r] = 0.0f;
+                        if (MODE == MODE_J4 && ((vmask >> (4 * s + t)) & 1u))
+                            mv4[s & 1][t][r] = __ldg(P.vin + (int64_t)r * P.nvox + vo);
+                    }
                 }
             }
 
@@ -296,7 +366,7 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
             // ---- stage: lane l prepares row e0 + l
             const int64_t e = e0 + lane;
             const bool have = e < item.e1;
-            bool ok0 = false, ok1 = false, in0 = false, in1 = false;
+            uint32_t okb = 0, inb = 0;   // sub-bricks the row may reach / lying between its transducer planes
             if (have) {
                 const int p = P.tile_rows[e];
                 const float4 base = P.ebase[e];
@@ -318,35 +388,43 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
                 const float dy = fmaf((float)TY, hb, bc.org[1]) - r.a.y;
                 const float dz = fmaf((float)TZ, hb, bc.org[2]) - r.a.z;
                 const float cx = fmaf(8.0f * wx + 3.5f, hb, dx);
-                const float cz = fmaf(4.0f * wz + 1.5f, hb, dz);
-                const float cy0 = fmaf(8.0f * wy + 1.5f, hb, dy);
-                const float cy1 = fmaf(8.0f * wy + 5.5f, hb, dy);
                 const float hxx = 3.5f * hb, hyy = 1.5f * hb;
                 // rows with zero weight add exactly nothing to J^T: skip them
                 const bool live = (MODE == MODE_JT4) ? (W4.x != 0.0f || W4.y != 0.0f || W4.z != 0.0f || W4.w != 0.0f)
                                                      : ((MODE != MODE_JT && MODE != MODE_COV) || (W != 0.0f));
-                ok0 = live && sub_ok0 && box_may_touch(cx, cy0, cz, ex, ey, ez, hl, hxx, hyy, hyy);
-                ok1 = live && sub_ok1 && box_may_touch(cx, cy1, cz, ex, ey, ez, hl, hxx, hyy, hyy);
-                // sub-bricks whose voxels all satisfy |p| <= hl (between the transducer planes)
                 const float pext = hxx * fabsf(ex) + hyy * (fabsf(ey) + fabsf(ez)) + 1e-3f;
-                const float pcx = fmaf(cx, ex, cz * ez);
-                in0 = fabsf(fmaf(cy0, ey, pcx)) + pext <= hl;
-                in1 = fabsf(fmaf(cy1, ey, pcx)) + pext <= hl;
+#pragma unroll
+                for (int s = 0; s < NSUB; ++s) {
+                    const float cy = fmaf(8.0f * wy + (float)sub_dy<NSUB>(s) + 1.5f, hb, dy);
+                    const float cz = fmaf(4.0f * wz + (float)sub_dz<NSUB>(s) + 1.5f, hb, dz);
+                    if (live && ((sub_ok >> s) & 1u) && box_may_touch(cx, cy, cz, ex, ey, ez, hl, hxx, hyy, hyy))
+                        okb |= 1u << s;
+                    // sub-bricks whose voxels all satisfy |p| <= hl (between the transducer planes)
+                    if (fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl) inb |= 1u << s;
+                }
                 const uint32_t tb = tab_addr + (uint32_t)(b * P.n_tab) * 8u - (PHI == PHI_TABLE ? MAGIC_BITS_X8 : 0u);
                 stg[lane * SR + 0] = base;
                 stg[lane * SR + 1] = make_float4(hb * ex, hb * ey, hb * ez, base3);
                 if (MODE == MODE_JT4) stg[lane * SR + 3] = W4;
                 // planar pair (both transducers at one z): stepping along x changes only c3
                 const int planar = (ez == 0.0f) ? 1 : 0;
+                // flags word: band (bits 0-7), sharp band (8), planar pair (9); with four
+                // sub-bricks also the sub-bricks the row may reach (12 + s) and the inner ones
+                // (16 + s)
+                const uint32_t fl = FLAGW ? ((okb << 12) | (inb << 16)) : 0u;
                 stg[lane * SR + 2] = make_float4(W, __uint_as_float(tb), __int_as_float(p),
-                                                __int_as_float(b | (bc.sharp << 8) | (planar << 9)));
+                                                __int_as_float(b | (bc.sharp << 8) | (planar << 9) | (int)fl));
             }
-            const uint32_t m0 = __ballot_sync(0xffffffffu, ok0);
-            const uint32_t m1 = __ballot_sync(0xffffffffu, ok1);
-            const uint32_t i0 = __ballot_sync(0xffffffffu, in0);
-            const uint32_t i1 = __ballot_sync(0xffffffffu, in1);
+            // With two sub-bricks the per-row tests read warp-uniform ballots (uniform branches);
+            // with four, the row's staged flag word (eight ballots per chunk cost more there).
+            uint32_t mk[NSUB], ik[NSUB];
+#pragma unroll
+            for (int s = 0; s < NSUB; ++s) {
+                mk[s] = FLAGW ? 0u : __ballot_sync(0xffffffffu, (okb >> s) & 1u);
+                ik[s] = FLAGW ? 0u : __ballot_sync(0xffffffffu, (inb >> s) & 1u);
+            }
+            uint32_t mm = __ballot_sync(0xffffffffu, okb != 0u);
             __syncwarp();
-            uint32_t mm = m0 | m1;
             float mypart = 0.0f;
             float mypart4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             while (mm) {
@@ -360,17 +438,19 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
                 const float hx = B.x, hy = B.y, hz = B.z, W = C.x;
                 const float hl = 0.5f * (A.x - A.y);   // used by the textbook (NAIVE) detour only
                 const uint32_t tb = __float_as_uint(C.y);
+                const uint32_t cw = (uint32_t)__float_as_int(C.w);
                 // voxels whose FP32 detour falls within CUT_BAND of a sharp band's cut-off
-                const float cutb = (SHARP && ((__float_as_int(C.w) >> 8) & 1)) ? CUT_BAND : -1.0f;
-                const bool planar = (DT != FFT_DT_FP64) && ((__float_as_int(C.w) >> 9) & 1);
+                const float cutb = (SHARP && ((cw >> 8) & 1u)) ? CUT_BAND : -1.0f;
+                const bool planar = (DT != FFT_DT_FP64) && ((cw >> 9) & 1u);
                 bool near = false;   // a voxel of this lane has its FP32 detour within CUT_BAND of the cut
                 // lane base (sub-brick 0, t = 0) in the pair frame: small offsets added to the
                 // tile origin's FP64-derived values
                 float part = 0.0f;
                 float part4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                 // The entry's evaluation, specialised for planar pairs (both transducers at one
-                // z: the axis has no z component, so h_z = 0 exactly and c1, c2 do not change
-                // along the lane's voxels or between the two sub-bricks).
+                // z: the axis has no z component, so h_z = 0 exactly, c1 and c2 do not change
+                // along the lane's voxels or between sub-bricks at one z, and p does not change
+                // in z).
                 // SH: the near-cut checks, only for rows of a band whose Phi does not vanish at
                 // the cut (the other rows of a sharp geometry take the plain evaluation; both
                 // give the same values there).
@@ -380,21 +460,19 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
                 const float off = PL ? fmaf(Xl, hx, Yl * hy) : fmaf(Xl, hx, fmaf(Yl, hy, Zl * hz));
                 float psb = A.x + off, prb = A.y + off;
                 float c1 = PL ? fmaf(-Zl, hy, A.z) : fmaf(Yl, hz, fmaf(-Zl, hy, A.z));
-                const float c2 = PL ? fmaf(Zl, hx, A.w) : fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
+                float c2 = PL ? fmaf(Zl, hx, A.w) : fmaf(Zl, hx, fmaf(-Xl, hz, A.w));
                 float c3 = fmaf(Xl, hy, fmaf(-Yl, hx, B.w));
-                const float c12_planar = PL ? fmaf(c2, c2, c1 * c1) : 0.0f;
+                float c12_planar = PL ? fmaf(c2, c2, c1 * c1) : 0.0f;
 #pragma unroll
-                for (int s = 0; s < 2; ++s) {
-                    const uint32_t ms = s ? m1 : m0;
-                    if (s == 1) {
-                        psb = fmaf(4.0f, hy, psb);
-                        prb = fmaf(4.0f, hy, prb);
-                        if (!PL) c1 = fmaf(4.0f, hz, c1);
-                        c3 = fmaf(-4.0f, hx, c3);
+                for (int s = 0; s < NSUB; ++s) {
+                    if (s > 0) {
+                        sub_step<NSUB, PL>(s, hx, hy, hz, psb, prb, c1, c2, c3);
+                        if (PL && s == 2) c12_planar = fmaf(c2, c2, c1 * c1);
                     }
-                    if (!((ms >> bit) & 1u)) continue;
+                    if (!(FLAGW ? ((cw >> (12 + s)) & 1u) : ((mk[s] >> bit) & 1u))) continue;
                     const float c1sq = PL ? 0.0f : c1 * c1;
-                    const bool inner = (DT == FFT_DT_STABLE) && (((s ? i1 : i0) >> bit) & 1u);
+                    const bool inner = (DT == FFT_DT_STABLE) &&
+                                       (FLAGW ? ((cw >> (16 + s)) & 1u) : ((ik[s] >> bit) & 1u));
 #define FFT_EVAL_SUB(INNER_V, PLANAR_V)                                                              \
     float vv[NX_LANE], ww[NX_LANE];                                                                \
     _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                          \
@@ -402,9 +480,9 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
         float is, ir, v, w;                                                                        \
         if (DT == FFT_DT_FP64) {                                                                   \
             const RowRec64 r64 = P.rec64[__float_as_int(C.z)];                                     \
-            const int b = __float_as_int(C.w) & 0xff;                                              \
-            v = detour_v64(r64, P.org[0], P.org[1], P.org[2], P.h, TX + oxi + t, TY + oyi + 4 * s, \
-                           TZ + ozi, P.bc[b].U, w);                                                \
+            const int b = (int)(cw & 0xffu);                                                       \
+            v = detour_v64(r64, P.org[0], P.org[1], P.org[2], P.h, TX + oxi + t,                   \
+                           TY + oyi + sub_dy<NSUB>(s), TZ + ozi + sub_dz<NSUB>(s), P.bc[b].U, w);  \
             is = 1.0f;                                                                             \
             ir = w;                                                                                \
         } else {                                                                                   \
@@ -442,10 +520,10 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
         if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                                  \
         if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val), W, acc[s][t]);                          \
         if (MODE == MODE_JT4) {                                                                    \
-            _Pragma("unroll") for (int r = 0; r < 4; ++r) acc4[s][t][r] = fmaf(val, Wr[r], acc4[s][t][r]); \
+            _Pragma("unroll") for (int r = 0; r < 4; ++r) acc4[s & 1][t][r] = fmaf(val, Wr[r], acc4[s & 1][t][r]); \
         }                                                                                          \
         if (MODE == MODE_J4) {                                                                     \
-            _Pragma("unroll") for (int r = 0; r < 4; ++r) part4[r] = fmaf(val, mv4[s][t][r], part4[r]); \
+            _Pragma("unroll") for (int r = 0; r < 4; ++r) part4[r] = fmaf(val, mv4[s & 1][t][r], part4[r]); \
         }                                                                                          \
         if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                      \
         if (MODE == MODE_FROB) {                                                                   \
@@ -460,10 +538,10 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
             if (MODE == MODE_JT) acc[s][t] = fmaf(val, W, acc[s][t]);                              \
             if (MODE == MODE_COV) acc[s][t] = fmaf(fabsf(val), W, acc[s][t]);                      \
             if (MODE == MODE_JT4) {                                                                \
-                _Pragma("unroll") for (int r = 0; r < 4; ++r) acc4[s][t][r] = fmaf(val, Wr[r], acc4[s][t][r]); \
+                _Pragma("unroll") for (int r = 0; r < 4; ++r) acc4[s & 1][t][r] = fmaf(val, Wr[r], acc4[s & 1][t][r]); \
             }                                                                                      \
             if (MODE == MODE_J4) {                                                                 \
-                _Pragma("unroll") for (int r = 0; r < 4; ++r) part4[r] = fmaf(val, mv4[s][t][r], part4[r]); \
+                _Pragma("unroll") for (int r = 0; r < 4; ++r) part4[r] = fmaf(val, mv4[s & 1][t][r], part4[r]); \
             }                                                                                      \
             if (MODE == MODE_J) part = fmaf(val, mv[s][t], part);                                  \
             if (MODE == MODE_FROB) {                                                               \
@@ -494,13 +572,18 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
                 if (SHARP && DT != FFT_DT_FP64 && __any_sync(0xffffffffu, near)) {
                     // FP64 re-decision of the voxels whose FP32 detour lies within CUT_BAND of
                     // the cut; d[k] is the change of this entry's term for voxel k = 4 s + t
-                    float d[8];
-                    if (near)
-                        sharp_fix<MODE, DT, GUARD, PHI>(P, A, B, C, Xl, Yl, Zl, planar, (i0 >> bit) & 1u,
-                                                        (i1 >> bit) & 1u, cutb, tb, nm1, nq, TX + oxi, TY + oyi,
-                                                        TZ + ozi, d);
+                    float d[4 * NSUB];
+                    uint32_t inner_bits = (cw >> 16) & 15u;
+                    if (!FLAGW) {
+                        inner_bits = 0u;
 #pragma unroll
-                    for (int s = 0; s < 2; ++s) {
+                        for (int s = 0; s < NSUB; ++s) inner_bits |= ((ik[s] >> bit) & 1u) << s;
+                    }
+                    if (near)
+                        sharp_fix<MODE, DT, GUARD, PHI, NSUB>(P, A, B, C, Xl, Yl, Zl, planar, inner_bits, cutb, tb, nm1,
+                                                              nq, TX + oxi, TY + oyi, TZ + ozi, d);
+#pragma unroll
+                    for (int s = 0; s < NSUB; ++s) {
 #pragma unroll
                         for (int t = 0; t < NX_LANE; ++t) {
                             const float dk = near ? d[4 * s + t] : 0.0f;
@@ -511,11 +594,11 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
                             if (MODE == MODE_J) part = fmaf(dk, mv[s][t], part);
                             if (MODE == MODE_JT4) {
 #pragma unroll
-                                for (int r = 0; r < 4; ++r) acc4[s][t][r] = fmaf(dk, Wr[r], acc4[s][t][r]);
+                                for (int r = 0; r < 4; ++r) acc4[s & 1][t][r] = fmaf(dk, Wr[r], acc4[s & 1][t][r]);
                             }
                             if (MODE == MODE_J4) {
 #pragma unroll
-                                for (int r = 0; r < 4; ++r) part4[r] = fmaf(dk, mv4[s][t][r], part4[r]);
+                                for (int r = 0; r < 4; ++r) part4[r] = fmaf(dk, mv4[s & 1][t][r], part4[r]);
                             }
                             if (MODE == MODE_FROB && valid) part += dk;
                         }
@@ -542,37 +625,42 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
             if (MODE == MODE_J) {
                 __syncwarp();
                 if (have) {
-                    if (((m0 | m1) >> lane) & 1u) {
+                    if (okb) {
                         const float4 r0 = stg[lane * SR + 0];
                         const float4 r1 = stg[lane * SR + 1];
                         const float Wl = stg[lane * SR + 2].x;
                         mypart = (r0.x + r0.y + r0.z + r0.w + r1.x + r1.y + r1.z + r1.w) * Wl;
                     }
-                    P.vout[e * 8 + region] = mypart;
+                    P.vout[e * NREG + region] = mypart;
                 }
             }
             if (MODE == MODE_J4 && have)
-                *reinterpret_cast<float4*>(P.vout + (e * 8 + region) * 4) =
+                *reinterpret_cast<float4*>(P.vout + (e * NREG + region) * 4) =
                     make_float4(mypart4[0], mypart4[1], mypart4[2], mypart4[3]);
             __syncwarp();
         }
 
         if (MODE == MODE_JT || MODE == MODE_COV) {
+            const uint32_t vm = lane_vmask();
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < NSUB; ++s) {
+                const int dy = sub_dy<NSUB>(s), dz = sub_dz<NSUB>(s);
                 if (item.slot < 0) {
 #pragma unroll
                     for (int t = 0; t < NX_LANE; ++t)
-                        if ((vmask >> (4 * s + t)) & 1u) P.vout[vbase + (int64_t)(4 * s) * P.nx + t] = acc[s][t];
+                        if ((vm >> (4 * s + t)) & 1u)
+                            P.vout[vbase + ((int64_t)dz * P.ny + dy) * P.nx + t] = acc[s][t];
                 } else {
                     // local index inside the tile: (z * 16 + y) * 16 + x
-                    const int loc = ((ozi * TILE_Y) + oyi + 4 * s) * TILE_X + oxi;
+                    const int loc = (((ozi + dz) * TILE_Y) + oyi + dy) * TILE_X + oxi;
                     float4 v4 = make_float4(acc[s][0], acc[s][1], acc[s][2], acc[s][3]);
                     *reinterpret_cast<float4*>(P.gpart + (int64_t)item.slot * TILE_VOX + loc) = v4;
                 }
             }
         }
         if (MODE == MODE_JT4) {
+            static_assert(!BATCH || NSUB == 2, "the four-column modes take 8 x 8 x 4 regions");
+            const uint32_t vm = lane_vmask();
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 const int loc = ((ozi * TILE_Y) + oyi + 4 * s) * TILE_X + oxi;
@@ -581,7 +669,7 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
                     if (item.slot < 0) {
 #pragma unroll
                         for (int t = 0; t < NX_LANE; ++t)
-                            if ((vmask >> (4 * s + t)) & 1u)
+                            if ((vm >> (4 * s + t)) & 1u)
                                 P.vout[(int64_t)r * P.nvox + vbase + (int64_t)(4 * s) * P.nx + t] = acc4[s][t][r];
                     } else {
                         float4 v4 = make_float4(acc4[s][0][r], acc4[s][1][r], acc4[s][2][r], acc4[s][3][r]);
@@ -608,12 +696,12 @@ __global__ void __launch_bounds__(apply_block_bound<MODE, DT, SHARP, PHI>(),
     }
 }
 
-// d_p = sum over the row's entries (ascending tile order) and the 8 warps of the partials.
+// d_p = sum over the row's entries (ascending tile order) and the 4 regions of the partials.
 __global__ void __launch_bounds__(256) j_reduce_kernel(const int64_t* __restrict__ row_off,
                                                        const int64_t* __restrict__ row_ent,
                                                        const float* __restrict__ jpart, int64_t M,
                                                        float* __restrict__ d) {
-    // one warp per row: lane l takes the row's entries l, l + 32, ... in order (the 8 region
+    // one warp per row: lane l takes the row's entries l, l + 32, ... in order (the 4 region
     // partials of an entry pairwise in FP32, entries accumulated in FP64), then a fixed
     // butterfly over the lanes; the order never depends on scheduling
     const int lane = threadIdx.x & 31;
@@ -623,16 +711,14 @@ __global__ void __launch_bounds__(256) j_reduce_kernel(const int64_t* __restrict
     const int64_t j1 = row_off[p + 1];
     int64_t j = row_off[p] + lane;
     for (; j + 32 < j1; j += 64) {   // two entries in flight, added in the same order
-        const float4* q0 = reinterpret_cast<const float4*>(jpart + row_ent[j] * 8);
-        const float4* q1 = reinterpret_cast<const float4*>(jpart + row_ent[j + 32] * 8);
-        const float4 a0 = __ldg(q0), b0 = __ldg(q0 + 1), a1 = __ldg(q1), b1 = __ldg(q1 + 1);
-        s += (double)(((a0.x + a0.y) + (a0.z + a0.w)) + ((b0.x + b0.y) + (b0.z + b0.w)));
-        s += (double)(((a1.x + a1.y) + (a1.z + a1.w)) + ((b1.x + b1.y) + (b1.z + b1.w)));
+        const float4 a0 = __ldg(reinterpret_cast<const float4*>(jpart + row_ent[j] * 4));
+        const float4 a1 = __ldg(reinterpret_cast<const float4*>(jpart + row_ent[j + 32] * 4));
+        s += (double)((a0.x + a0.y) + (a0.z + a0.w));
+        s += (double)((a1.x + a1.y) + (a1.z + a1.w));
     }
     if (j < j1) {
-        const float4* q = reinterpret_cast<const float4*>(jpart + row_ent[j] * 8);
-        const float4 a = __ldg(q), b = __ldg(q + 1);
-        s += (double)(((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w)));
+        const float4 a = __ldg(reinterpret_cast<const float4*>(jpart + row_ent[j] * 4));
+        s += (double)((a.x + a.y) + (a.z + a.w));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -924,7 +1010,7 @@ static void launch_split(fft_geom g, const ApplyParams& P, cudaStream_t st) {
         Q.items = P.items + np;
         Q.n_items = ns;
         Q.counter = P.counter + 1;
-        if (Q.dsum) Q.dsum = P.dsum + (size_t)np * 8;   // per-unit partials follow the plain launch's
+        if (Q.dsum) Q.dsum = P.dsum + (size_t)np * apply_regions<MODE>();   // per-unit partials follow the plain launch's
         launch_apply<MODE, DT, G, true, PHI>(g, Q, st);
     }
 }

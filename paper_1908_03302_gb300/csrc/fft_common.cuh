@@ -134,7 +134,7 @@ struct fft_geom_s {
     int32_t n_slots = 0;
     int32_t* tile_slot0 = nullptr;       // [n_tiles] first slot of a multi-item tile, -1 single, -2 none
     int32_t* tile_nslot = nullptr;       // [n_tiles]
-    float* jpart = nullptr;              // [E * 8]
+    float* jpart = nullptr;              // [E * 4]
     float* gpart = nullptr;              // [n_slots * TILE_VOX]
     int32_t* counter = nullptr;          // [4] work counters
     int64_t support = 0;

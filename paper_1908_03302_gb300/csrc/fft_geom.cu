@@ -653,7 +653,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
     g->apply_ctas = apply_occupancy(g);
     sharp_launch_shape(g);
     plain_launch_shape(g);
-    GEOM_TRY(dmalloc(g, &g->jpart, (size_t)g->E * APPLY_WARPS));
+    GEOM_TRY(dmalloc(g, &g->jpart, (size_t)g->E * 4));   // one J partial per (entry, 8 x 8 x 8 region)
     GEOM_TRY(dmalloc(g, &g->counter, 4));
     GEOM_TRY(build_items(g, toff, DEFAULT_ITEMS_PER_CTA));
     GEOM_CUDA(cudaDeviceSynchronize());
