@@ -51,9 +51,9 @@ FP32_LANES_PER_SM_CLK = 128
 # workload, from ncu captures of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum); a workload without a capture of the current build reports null.
 APPLY_TRAFFIC_BYTES = {
-    # plain-band apply 4025283072 + 151932160, sharp-band apply 5192666624 + 385817856,
-    # jt_reduce 342402304 + 6704640
-    "slices3d": 10104806656,
+    # plain-band apply 3910192640 + 149975552, sharp-band apply 5340387840 + 374120960,
+    # jt_reduce 342418176 + 6821632
+    "slices3d": 10123916800,
 }
 
 
