@@ -60,6 +60,10 @@ constexpr int RING = 8;                // chunks of staged rows between the scan
 constexpr int D_LANES = 16;            // lanes that scatter one row's D entries
 constexpr long long WAIT_BUDGET = 4000000000ll;   // cycles (~2 s)
 constexpr int HDR_FIRST = 1, HDR_LAST = 2;         // chunk header flags
+constexpr int MAX_B_ROWS = 512;                    // N of the two MMAs per K step together
+
+// Zero page the MMA warp copies over a consumed B tile (static storage: zero-initialised).
+__device__ __align__(128) uint4 g_zero_b[MAX_B_ROWS * KC * 2 / 16];
 
 struct PsfTcParams {
     const RowRec* rec;
@@ -105,7 +109,7 @@ struct ChunkHdr {
 struct TcShared {
     unsigned long long full[NSTAGE];       // generator warps -> MMA warp (GEN_WARPS arrivals)
     unsigned long long done[NSTAGE];       // tensor cores -> MMA warp and epilogue (tcgen05.commit)
-    unsigned long long empty[NSTAGE];      // MMA warp -> generator warps (B tile cleared; 32 arrivals)
+    unsigned long long empty[NSTAGE];      // MMA warp -> generator warps (B tile zero-filled: 1 arrival + bytes)
     unsigned long long ring_full[RING];    // scan warps -> generator and MMA warps (1 arrival)
     unsigned long long ring_empty[RING];   // generator and MMA warps -> scan warps (GEN_WARPS + 1)
     unsigned long long tmem_free;          // epilogue read the accumulator -> MMA warp (GEN_WARPS)
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         for (int b = 0; b < NSTAGE; ++b) {
             tc::mbar_init(full0 + 8u * b, GEN_WARPS);
             tc::mbar_init(done0 + 8u * b, 1);
-            tc::mbar_init(empty0 + 8u * b, 32);
+            tc::mbar_init(empty0 + 8u * b, 1);
         }
         for (int b = 0; b < RING; ++b) {
             tc::mbar_init(ring_full0 + 8u * b, 1);
@@ -437,13 +441,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         }
     } else if (warp < GEN_WARPS) {
         // ================= generator warps
-        // Warp w evaluates rows 2w and 2w + 1 of a chunk; lane l owns the four consecutive x
-        // voxels (4 lx + t, ly, lz), t = 0..3, of the 8 x 4 x 4 sub-brick, with lx = l & 1,
-        // ly = (l >> 1) & 3, lz = l >> 3. Voxel t of lane l is MMA row (TMEM lane) m = 32 t + l,
-        // which spreads a warp's stores over all eight 16-byte slots of a core matrix. For D the
-        // warp owns B-tile rows 2w (lanes 0-15) and 2w + 1 (lanes 16-31) of every stage; lane i
-        // of a half scatters the row's D entries i, i + 16, i + 32, ...
-        const int glx = lane & 1, gly = (lane >> 1) & 3, glz = lane >> 3;
+        // Warp w covers rows 8 (w % 6) .. 8 (w % 6) + 7 of a chunk and the z layer q = w / 6 of
+        // the 8 x 4 x 4 sub-brick. Lane l evaluates rows k0 = 8 (w % 6) + 2 (l >> 3) and k0 + 1 on
+        // the four consecutive x voxels (4 (g & 1) + t, (g >> 1) & 3, q), t = 0..3, g = l & 7.
+        // Voxel t of lane l is MMA row (TMEM lane) m = 32 q + 8 t + g: one store instruction
+        // then writes eight rows m and four K pairs of one core matrix, 32 distinct banks. For
+        // D the warp owns B-tile rows 2w (lanes 0-15) and 2w + 1 (lanes 16-31) of every stage;
+        // lane i of a half scatters the row's D entries i, i + 16, i + 32, ... scaled by the
+        // row's constant C_p (so the A tile holds Phi / (R_xs R_xr) alone).
+        static_assert(KC == 8 * (GEN_WARPS / 4) && GEN_WARPS % 4 == 0, "generator warps: 8 rows x 4 z layers");
+        const int gq = warp / (GEN_WARPS / 4), gk0 = 8 * (warp % (GEN_WARPS / 4)) + 2 * (lane >> 3);
+        const int gg = lane & 7;
         const int d_r = 2 * warp + (lane >> 4), d_i0 = lane & (D_LANES - 1);
         for (;; ++chunk) {
             const int slot = chunk % RING;
@@ -464,8 +472,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             // D entries of this lane's B row: loads issued now, stored after the generation
             uint32_t d_beg = 0;
             int d_cnt = 0;
+            float d_w = 0.0f;
             if (d_r < nrows) {
                 const float4 C = stg[d_r * 3 + 2];
+                d_w = C.x;
                 d_beg = __float_as_uint(C.z);
                 d_cnt = __float_as_int(C.w);
             }
@@ -485,12 +495,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                 failed = true;
                 break;
             }
-            // generate A: rows 2 warp, 2 warp + 1; this lane's four voxels
-            const float Xv = (float)(SX + 4 * glx), Yv = (float)(SY + gly), Zv = (float)(SZ + glz);
+            // generate A: this lane's rows gk0, gk0 + 1 on its four voxels. The detour form is
+            // chosen per warp: the inner / planar forms only where all eight rows allow them.
+            const float Xv = (float)(SX + 4 * (gg & 1)), Yv = (float)(SY + ((gg >> 1) & 3)), Zv = (float)(SZ + gq);
+            uint32_t fl = 3u;
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+                if (gk0 + rr < nrows) fl &= __float_as_uint(stg[(gk0 + rr) * 3 + 2].y) & 3u;
+            const uint32_t wfl = (__all_sync(0xffffffffu, fl & 1u) ? 1u : 0u) | (__all_sync(0xffffffffu, fl & 2u) ? 2u : 0u);
             float vals[2][NX_LANE];
 #pragma unroll
             for (int rr = 0; rr < 2; ++rr) {
-                const int r = 2 * warp + rr;
+                const int r = gk0 + rr;
                 if (r < nrows) {
                     const float4 A4 = stg[r * 3 + 0];
                     const float4 B4 = stg[r * 3 + 1];
@@ -503,8 +519,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                     const float c3 = fmaf(Xv, hy, fmaf(-Yv, hx, B4.w));
                     const float c1sq = c1 * c1;
                     const float c12sq = fmaf(c2, c2, c1sq);
-                    const uint32_t tbf = __float_as_uint(C4.y);
-                    const uint32_t tb = tbf & ~3u;
+                    const uint32_t tbf = wfl;
+                    const uint32_t tb = __float_as_uint(C4.y) & ~3u;
                     // warp-uniform choice of the detour form for the whole run of voxels
 #define FFT_TC_RUN(INNER_V, PLANAR_V)                                                              \
     _Pragma("unroll") for (int t = 0; t < NX_LANE; ++t) {                                        \
@@ -520,7 +536,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         }                                                                                        \
         float is, ir;                                                                            \
         const float v = detour_v<FFT_DT_STABLE, GUARD, INNER_V>(pst, prt, q2, 0.0f, is, ir);     \
-        vals[rr][t] = phi_lookup(v, tb, nm1) * (is * ir) * C4.x;                                 \
+        vals[rr][t] = phi_lookup(v, tb, nm1) * (is * ir);                                        \
     }
                     if (tbf & 1u) {
                         if (tbf & 2u) {
@@ -543,16 +559,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             }
 #pragma unroll
             for (int t = 0; t < NX_LANE; ++t)
-                *reinterpret_cast<uint32_t*>(sA + tc::kmajor_offset((uint32_t)(32 * t + lane), (uint32_t)(2 * warp), KC)) =
+                *reinterpret_cast<uint32_t*>(sA + tc::kmajor_offset((uint32_t)(32 * gq + 8 * t + gg), (uint32_t)gk0, KC)) =
                     pack_bf16x2(vals[0][t], vals[1][t]);
-            // B: the stage was cleared by the MMA warp; scatter this row's D entries
+            // B: the stage was zero-filled (bulk copy issued by the MMA warp); scatter this row's
+            // D entries times C_p
             if (has0)
-                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j0, (uint32_t)d_r, KC)) = __float2bfloat16_rn(dv0);
+                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j0, (uint32_t)d_r, KC)) =
+                    __float2bfloat16_rn(dv0 * d_w);
             if (has1)
-                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j1, (uint32_t)d_r, KC)) = __float2bfloat16_rn(dv1);
+                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j1, (uint32_t)d_r, KC)) =
+                    __float2bfloat16_rn(dv1 * d_w);
             for (int i = d_i0 + 2 * D_LANES; i < d_cnt; i += D_LANES)   // long rows
                 *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)P.d_idx[d_beg + i], (uint32_t)d_r, KC)) =
-                    __float2bfloat16_rn(P.d_val[d_beg + i]);
+                    __float2bfloat16_rn(P.d_val[d_beg + i] * d_w);
             // publish this warp's part of the chunk to the MMA warp; release the ring slot
             tc::fence_proxy_async_smem();
             __syncwarp();
@@ -569,9 +588,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                 tc::fence_after_sync();
                 const int tx = T % P.tiles_x, ty = (T / P.tiles_x) % P.tiles_y, tz = T / (P.tiles_x * P.tiles_y);
                 const int X0 = TILE_X * tx + SX, Y0 = TILE_Y * ty + SY, Z0 = TILE_Z * tz + SZ;
-                const int quarter = warp & 3;   // TMEM lanes this warp may access
-                // TMEM lane 32 quarter + lane holds voxel t = quarter of generation lane `lane`
-                const int x = X0 + 4 * (lane & 1) + quarter, y = Y0 + ((lane >> 1) & 3), z = Z0 + (lane >> 3);
+                const int quarter = warp & 3;   // TMEM lanes this warp may access (z layer)
+                // TMEM lane m = 32 quarter + lane holds voxel (4 (g & 1) + t, (g >> 1) & 3, quarter)
+                // with t = lane >> 3, g = lane & 7 (the generators' row order)
+                const int eg = lane & 7;
+                const int x = X0 + 4 * (eg & 1) + (lane >> 3), y = Y0 + ((eg >> 1) & 3), z = Z0 + quarter;
                 const bool valid = x < P.nx && y < P.ny && z < P.nz;
                 const int64_t v = ((int64_t)z * P.ny + y) * P.nx + x;
                 const int cols = P.nh * P.n_half;
@@ -592,7 +613,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
     } else {
         // ================= MMA warp
         const uint32_t idesc = tc::idesc_bf16(128, (uint32_t)P.n_half);
-        int units = 0;   // units whose first chunk was issued
+        int units = 0;    // units whose first chunk was issued
+        int copied = 0;   // chunks whose B stage got its zero-fill copy (0 .. copied - 1)
         for (;; ++chunk) {
             const int slot = chunk % RING;
             if (!warp_wait(ring_full0 + 8u * slot, (uint32_t)((chunk / RING) & 1), lane, P.status)) {
@@ -632,7 +654,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             }
             __syncwarp();
             // the previous chunk's MMAs are done (they complete in order, before this chunk's):
-            // clear its B tile and hand the stage back to the generators
+            // zero its B tile with a bulk copy from a zero page in global memory, which
+            // completes the stage's "empty" phase when its bytes have landed
             if (chunk > 0) {
                 const int prev = chunk - 1;
                 const int pbuf = prev % NSTAGE;
@@ -641,10 +664,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                     break;
                 }
                 tc::fence_after_sync();
-                uint4* b4 = reinterpret_cast<uint4*>(sB0 + pbuf * b_bytes);
-                for (uint32_t i = lane; i < b_bytes / 16; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
-                tc::fence_proxy_async_smem();
-                tc::mbar_arrive(empty0 + 8u * pbuf);
+                if (lane == 0) {
+                    tc::mbar_arrive_expect_tx(empty0 + 8u * pbuf, b_bytes);
+                    tc::bulk_copy_g2s(smem_addr(sB0 + pbuf * b_bytes), g_zero_b, b_bytes, empty0 + 8u * pbuf);
+                }
+                copied = chunk;
+                __syncwarp();
             }
         }
         // drain: every issued MMA must be complete before the accumulator is released
@@ -653,6 +678,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             if (lane == 0) wait_phase(done0 + 8u * (last % NSTAGE), (uint32_t)((last / NSTAGE) & 1));
             __syncwarp();
         }
+        // and every zero-fill copy must have landed before the CTA's shared memory goes away:
+        // the last copy into each stage is that stage's latest "empty" phase
+        if (lane == 0)
+            for (int c = copied > NSTAGE ? copied - NSTAGE : 0; c < copied; ++c)
+                wait_phase(empty0 + 8u * (c % NSTAGE), (uint32_t)((c / NSTAGE) & 1));
+        __syncwarp();
         if (lane == 0 && chunk > 0) atomicAdd(P.chunks, (unsigned long long)chunk);
     }
     tc::fence_before_sync();
@@ -757,6 +788,10 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     P.n_half = n_half;
     P.nh = nh;
     P.b_rows = nh * n_half;
+    if (P.b_rows > MAX_B_ROWS) {   // cannot happen for n_rhs <= 512; the zero page is sized by it
+        set_error("psf tensor-core path: B tile larger than its zero page");
+        return FFT_ERR_ARG;
+    }
     P.tmem_cols = tmem_cols;
     P.out = out;
     P.V = g->V;

@@ -103,6 +103,21 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
         : "memory");
 }
 
+// One arrival that also announces `bytes` of asynchronous-copy traffic the current phase must
+// receive before it completes.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Bulk asynchronous copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from
+// global to shared memory, counted as transaction bytes on the mbarrier at `mbar`.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst_smem),
+        "l"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
 // Bounded wait for the phase with the given parity; returns false if it did not complete
 // within `max_iter` polls (the caller then records an error instead of hanging).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, uint32_t max_iter) {
