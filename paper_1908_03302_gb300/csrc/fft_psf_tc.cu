@@ -49,12 +49,15 @@ namespace fftgb {
 
 namespace {
 
-constexpr int GEN_WARPS = 24;          // warps that generate J and scatter D (warps 0 .. 23)
+constexpr int KC = 48;                 // rows per chunk (MMA K per chunk)
+// rows a generator lane evaluates per chunk (even). Measured on psf3d: 2 rows in 24 warps
+// 914 ms, 4 rows in 12 warps 1036 ms (fewer warps to hide the evaluation chains' latency).
+constexpr int GEN_ROWS = 2;
+constexpr int GEN_WARPS = KC / GEN_ROWS;   // warps that generate J and scatter D (warps 0 ..)
 constexpr int SCAN_WARPS = 2;          // warps that scan candidate rows (warps 24, 25)
 constexpr int MMA_WARP = GEN_WARPS + SCAN_WARPS;   // the warp that issues the MMAs
 constexpr int TC_WARPS = MMA_WARP + 1;
 constexpr int TC_THREADS = TC_WARPS * 32;
-constexpr int KC = 2 * GEN_WARPS;      // rows per chunk (MMA K per chunk): 2 per generator warp
 constexpr int NSTAGE = 3;              // A / B stages
 constexpr int RING = 8;                // chunks of staged rows between the scan and the generation
 constexpr int D_LANES = 16;            // lanes that scatter one row's D entries
@@ -441,18 +444,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         }
     } else if (warp < GEN_WARPS) {
         // ================= generator warps
-        // Warp w covers rows 8 (w % 6) .. 8 (w % 6) + 7 of a chunk and the z layer q = w / 6 of
-        // the 8 x 4 x 4 sub-brick. Lane l evaluates rows k0 = 8 (w % 6) + 2 (l >> 3) and k0 + 1 on
-        // the four consecutive x voxels (4 (g & 1) + t, (g >> 1) & 3, q), t = 0..3, g = l & 7.
-        // Voxel t of lane l is MMA row (TMEM lane) m = 32 q + 8 t + g: one store instruction
-        // then writes eight rows m and four K pairs of one core matrix, 32 distinct banks. For
-        // D the warp owns B-tile rows 2w (lanes 0-15) and 2w + 1 (lanes 16-31) of every stage;
-        // lane i of a half scatters the row's D entries i, i + 16, i + 32, ... scaled by the
-        // row's constant C_p (so the A tile holds Phi / (R_xs R_xr) alone).
-        static_assert(KC == 8 * (GEN_WARPS / 4) && GEN_WARPS % 4 == 0, "generator warps: 8 rows x 4 z layers");
-        const int gq = warp / (GEN_WARPS / 4), gk0 = 8 * (warp % (GEN_WARPS / 4)) + 2 * (lane >> 3);
+        // With W = GEN_WARPS / 4 warps per z layer, warp w covers rows 4 GEN_ROWS (w % W) ..
+        // 4 GEN_ROWS (w % W) + 4 GEN_ROWS - 1 of a chunk and the z layer q = w / W of the 8 x 4 x 4
+        // sub-brick. Lane l evaluates the rows k0 + 8 pi and k0 + 8 pi + 1 (pi < GEN_ROWS / 2,
+        // k0 = 4 GEN_ROWS (w % W) + 2 (l >> 3)) on the four consecutive x voxels
+        // (4 (g & 1) + t, (g >> 1) & 3, q), t = 0..3, g = l & 7. Voxel t of lane l is MMA row (TMEM
+        // lane) m = 32 q + 8 t + g: one store instruction then writes eight rows m and four K
+        // pairs of one core matrix, 32 distinct banks. For D the warp owns B-tile rows
+        // GEN_ROWS w .. GEN_ROWS w + GEN_ROWS - 1 of every stage, two at a time (lanes 0-15 and
+        // 16-31); lane i of a half scatters the row's D entries i, i + 16, i + 32, ... scaled by
+        // the row's constant C_p (so the A tile holds Phi / (R_xs R_xr) alone).
+        static_assert(KC == 4 * GEN_ROWS * (GEN_WARPS / 4) && GEN_WARPS % 4 == 0 && GEN_ROWS % 2 == 0,
+                      "generator warps: 4 GEN_ROWS rows x 4 z layers");
+        constexpr int GP = GEN_ROWS / 2;   // row pairs per lane
+        const int gq = warp / (GEN_WARPS / 4), gk0 = 4 * GEN_ROWS * (warp % (GEN_WARPS / 4)) + 2 * (lane >> 3);
         const int gg = lane & 7;
-        const int d_r = 2 * warp + (lane >> 4), d_i0 = lane & (D_LANES - 1);
+        const int d_i0 = lane & (D_LANES - 1);
         for (;; ++chunk) {
             const int slot = chunk % RING;
             if (!warp_wait(ring_full0 + 8u * slot, (uint32_t)((chunk / RING) & 1), lane, P.status)) {
@@ -469,44 +476,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             const uint32_t use = (uint32_t)(chunk / NSTAGE);
             unsigned char* sA = sA0 + buf * a_bytes;
             unsigned char* sB = sB0 + buf * b_bytes;
-            // D entries of this lane's B row: loads issued now, stored after the generation
-            uint32_t d_beg = 0;
-            int d_cnt = 0;
-            float d_w = 0.0f;
-            if (d_r < nrows) {
-                const float4 C = stg[d_r * 3 + 2];
-                d_w = C.x;
-                d_beg = __float_as_uint(C.z);
-                d_cnt = __float_as_int(C.w);
-            }
-            const bool has0 = d_i0 < d_cnt, has1 = d_i0 + D_LANES < d_cnt;
-            uint32_t j0 = 0, j1 = 0;
-            float dv0 = 0.0f, dv1 = 0.0f;
-            if (has0) {
-                j0 = P.d_idx[d_beg + d_i0];
-                dv0 = P.d_val[d_beg + d_i0];
-            }
-            if (has1) {
-                j1 = P.d_idx[d_beg + d_i0 + D_LANES];
-                dv1 = P.d_val[d_beg + d_i0 + D_LANES];
+            // D entries of this warp's B rows GEN_ROWS w + 2 dp + (lane >> 4): loads issued now,
+            // stored after the generation
+            int d_r[GP], d_cnt[GP];
+            uint32_t d_beg[GP], j0[GP], j1[GP];
+            float d_w[GP], dv0[GP], dv1[GP];
+#pragma unroll
+            for (int dp = 0; dp < GP; ++dp) {
+                d_r[dp] = GEN_ROWS * warp + 2 * dp + (lane >> 4);
+                d_beg[dp] = 0;
+                d_cnt[dp] = 0;
+                d_w[dp] = 0.0f;
+                if (d_r[dp] < nrows) {
+                    const float4 C = stg[d_r[dp] * 3 + 2];
+                    d_w[dp] = C.x;
+                    d_beg[dp] = __float_as_uint(C.z);
+                    d_cnt[dp] = __float_as_int(C.w);
+                }
+                j0[dp] = j1[dp] = 0;
+                dv0[dp] = dv1[dp] = 0.0f;
+                if (d_i0 < d_cnt[dp]) {
+                    j0[dp] = P.d_idx[d_beg[dp] + d_i0];
+                    dv0[dp] = P.d_val[d_beg[dp] + d_i0];
+                }
+                if (d_i0 + D_LANES < d_cnt[dp]) {
+                    j1[dp] = P.d_idx[d_beg[dp] + d_i0 + D_LANES];
+                    dv1[dp] = P.d_val[d_beg[dp] + d_i0 + D_LANES];
+                }
             }
             // the MMAs that last read this stage must be done and its B tile cleared
             if (chunk >= NSTAGE && !warp_wait(empty0 + 8u * buf, (use - 1u) & 1u, lane, P.status)) {
                 failed = true;
                 break;
             }
-            // generate A: this lane's rows gk0, gk0 + 1 on its four voxels. The detour form is
-            // chosen per warp: the inner / planar forms only where all eight rows allow them.
+            // generate A: this lane's rows gk0 + 8 pi + (0, 1) on its four voxels. The detour
+            // form is chosen per warp: the inner / planar forms only where all its rows allow them.
             const float Xv = (float)(SX + 4 * (gg & 1)), Yv = (float)(SY + ((gg >> 1) & 3)), Zv = (float)(SZ + gq);
             uint32_t fl = 3u;
 #pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
-                if (gk0 + rr < nrows) fl &= __float_as_uint(stg[(gk0 + rr) * 3 + 2].y) & 3u;
+            for (int rr = 0; rr < GEN_ROWS; ++rr) {
+                const int r = gk0 + 8 * (rr >> 1) + (rr & 1);
+                if (r < nrows) fl &= __float_as_uint(stg[r * 3 + 2].y) & 3u;
+            }
             const uint32_t wfl = (__all_sync(0xffffffffu, fl & 1u) ? 1u : 0u) | (__all_sync(0xffffffffu, fl & 2u) ? 2u : 0u);
-            float vals[2][NX_LANE];
+            float vals[GEN_ROWS][NX_LANE];
 #pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int r = gk0 + rr;
+            for (int rr = 0; rr < GEN_ROWS; ++rr) {
+                const int r = gk0 + 8 * (rr >> 1) + (rr & 1);
                 if (r < nrows) {
                     const float4 A4 = stg[r * 3 + 0];
                     const float4 B4 = stg[r * 3 + 1];
@@ -558,20 +574,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                 }
             }
 #pragma unroll
-            for (int t = 0; t < NX_LANE; ++t)
-                *reinterpret_cast<uint32_t*>(sA + tc::kmajor_offset((uint32_t)(32 * gq + 8 * t + gg), (uint32_t)gk0, KC)) =
-                    pack_bf16x2(vals[0][t], vals[1][t]);
-            // B: the stage was zero-filled (bulk copy issued by the MMA warp); scatter this row's
+            for (int pi = 0; pi < GP; ++pi)
+#pragma unroll
+                for (int t = 0; t < NX_LANE; ++t)
+                    *reinterpret_cast<uint32_t*>(
+                        sA + tc::kmajor_offset((uint32_t)(32 * gq + 8 * t + gg), (uint32_t)(gk0 + 8 * pi), KC)) =
+                        pack_bf16x2(vals[2 * pi][t], vals[2 * pi + 1][t]);
+            // B: the stage was zero-filled (bulk copy issued by the MMA warp); scatter the rows'
             // D entries times C_p
-            if (has0)
-                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j0, (uint32_t)d_r, KC)) =
-                    __float2bfloat16_rn(dv0 * d_w);
-            if (has1)
-                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j1, (uint32_t)d_r, KC)) =
-                    __float2bfloat16_rn(dv1 * d_w);
-            for (int i = d_i0 + 2 * D_LANES; i < d_cnt; i += D_LANES)   // long rows
-                *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)P.d_idx[d_beg + i], (uint32_t)d_r, KC)) =
-                    __float2bfloat16_rn(P.d_val[d_beg + i] * d_w);
+#pragma unroll
+            for (int dp = 0; dp < GP; ++dp) {
+                const uint32_t kr = (uint32_t)d_r[dp];
+                if (d_i0 < d_cnt[dp])
+                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j0[dp], kr, KC)) =
+                        __float2bfloat16_rn(dv0[dp] * d_w[dp]);
+                if (d_i0 + D_LANES < d_cnt[dp])
+                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(j1[dp], kr, KC)) =
+                        __float2bfloat16_rn(dv1[dp] * d_w[dp]);
+                for (int i = d_i0 + 2 * D_LANES; i < d_cnt[dp]; i += D_LANES)   // long rows
+                    *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset((uint32_t)P.d_idx[d_beg[dp] + i], kr, KC)) =
+                        __float2bfloat16_rn(P.d_val[d_beg[dp] + i] * d_w[dp]);
+            }
             // publish this warp's part of the chunk to the MMA warp; release the ring slot
             tc::fence_proxy_async_smem();
             __syncwarp();
