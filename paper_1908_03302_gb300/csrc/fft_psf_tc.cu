@@ -78,8 +78,8 @@ struct PsfTcParams {
     const int64_t* tile_off;
     const float4* ebase;
     const float* ebase3;
-    int32_t* c_ent;            // compact candidates of each tile (from tile_off[T]): entry id,
-    int32_t* c_row;            //   row,
+    float4* c_rec;             // compact candidates of each tile (from tile_off[T]): staging record
+                               //   (3 float4 per candidate, see psf_mask_kernel),
     uint16_t* c_mask;          //   sub-bricks the row may reach
     int32_t* c_cnt;            // compact candidates per tile
     const int32_t* units;      // (tile << 4) | sub-brick, heaviest tiles first
@@ -129,9 +129,13 @@ struct TcShared {
     int p_started;                         // the current unit has staged rows
 };
 
+// Bounded wait for a phase. Each poll lets the hardware suspend the thread for up to
+// WAIT_HINT_NS while the phase is incomplete, so that waiting warps leave the issue slots to
+// the generating ones.
+constexpr uint32_t WAIT_HINT_NS = 1000;
 __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
     const long long t0 = clock64();
-    while (!tc::mbar_try_wait(mbar, parity)) {
+    while (!tc::mbar_try_wait_sleep(mbar, parity, WAIT_HINT_NS)) {
         if (clock64() - t0 > WAIT_BUDGET) return false;
     }
     return true;
@@ -184,6 +188,11 @@ constexpr int MASK_THREADS = 256;
 // each with the mask of its 16 sub-bricks (8 x 4 x 4, inside the grid) that the row's support
 // may reach (tangent-plane bound of the convex detour, as in the J^T kernel), in candidate
 // order, written from tile_off[T]; c_cnt[T] their number and c_or[T] the union of the masks.
+// With each candidate goes its staging record, so that the scan warps gather one contiguous
+// record per kept row instead of chasing the entry, the row and its D offsets:
+//   r0 = the entry's tile-origin base (p + L/2, p - L/2, c1, c2) in the pair frame,
+//   r1 = (h e_x, h e_y, h e_z, c3) (pair-frame steps per voxel and the base's c3),
+//   r2 = (C_p, band index, first D entry of the row, D entries of the row) (bits).
 __global__ void __launch_bounds__(MASK_THREADS) psf_mask_kernel(const PsfTcParams P, uint16_t* __restrict__ c_or) {
     __shared__ int wsum[MASK_THREADS / 32];
     __shared__ unsigned int s_or;
@@ -198,13 +207,19 @@ __global__ void __launch_bounds__(MASK_THREADS) psf_mask_kernel(const PsfTcParam
     for (int64_t e0 = e_begin; e0 < e_end; e0 += MASK_THREADS) {
         const int64_t e = e0 + threadIdx.x;
         unsigned int mask = 0u;
-        int p = 0;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
         if (e < e_end) {
-            p = P.tile_rows[e];
-            if (P.d_off[p + 1] > P.d_off[p]) {   // rows without D entries add nothing
+            const int p = P.tile_rows[e];
+            const int64_t d0 = P.d_off[p], d1 = P.d_off[p + 1];
+            if (d1 > d0) {   // rows without D entries add nothing
                 const RowRec r = P.rec[p];
-                const BandConst bc = P.bc[P.row_band[p]];
+                const int bnd = P.row_band[p];
+                const BandConst bc = P.bc[bnd];
                 const float hb = bc.h;
+                r0 = P.ebase[e];
+                r1 = make_float4(hb * r.b.x, hb * r.b.y, hb * r.b.z, P.ebase3[e]);
+                r2 = make_float4(r.b.w, __int_as_float(bnd), __uint_as_float((uint32_t)d0),
+                                 __int_as_float((int)(d1 - d0)));
                 for (int sb = 0; sb < 16; ++sb) {
                     const int X0 = TILE_X * tx + 8 * (sb & 1), Y0 = TILE_Y * ty + 4 * ((sb >> 1) & 3),
                               Z0 = TILE_Z * tz + 4 * (sb >> 3);
@@ -229,8 +244,9 @@ __global__ void __launch_bounds__(MASK_THREADS) psf_mask_kernel(const PsfTcParam
         }
         if (keep) {
             const int64_t pos = base + before + __popc(bal & ((1u << lane) - 1u));
-            P.c_ent[pos] = (int32_t)e;
-            P.c_row[pos] = p;
+            P.c_rec[3 * pos + 0] = r0;
+            P.c_rec[3 * pos + 1] = r1;
+            P.c_rec[3 * pos + 2] = r2;
             P.c_mask[pos] = (uint16_t)mask;
         }
         base += total;
@@ -349,6 +365,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             const int X0 = TILE_X * tx + 8 * (sb & 1), Y0 = TILE_Y * ty + 4 * ((sb >> 1) & 3),
                       Z0 = TILE_Z * tz + 4 * (sb >> 3);
             const bool inside = X0 < P.nx && Y0 < P.ny && Z0 < P.nz;
+            const int SXo = 8 * (sb & 1), SYo = 4 * ((sb >> 1) & 3), SZo = 4 * (sb >> 3);   // in the tile
             const int64_t c_begin = P.tile_off[T];
             const int n_c = inside ? P.c_cnt[T] : 0;
             const int n_blocks = (n_c + 31) / 32;
@@ -357,29 +374,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                 const int ci = 32 * b + lane;
                 bool keep = false;
                 float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
-                if (ci < n_c && ((P.c_mask[c_begin + ci] >> sb) & 1u)) {
-                    keep = true;
-                    const int64_t e = P.c_ent[c_begin + ci];
-                    const int p = P.c_row[c_begin + ci];
-                    const int64_t d0 = P.d_off[p], d1 = P.d_off[p + 1];
-                    const RowRec r = P.rec[p];
-                    const int bnd = P.row_band[p];
-                    const BandConst bc = S.bc[bnd];
-                    const float hb = bc.h;
-                    const float ex = r.b.x, ey = r.b.y, ez = r.b.z, hl = r.a.w;
-                    const float cx = fmaf((float)(X0) + 3.5f, hb, bc.org[0]) - r.a.x;
-                    const float cy = fmaf((float)(Y0) + 1.5f, hb, bc.org[1]) - r.a.y;
-                    const float cz = fmaf((float)(Z0) + 1.5f, hb, bc.org[2]) - r.a.z;
-                    // is the whole sub-brick between the transducer planes? a planar pair?
-                    const float pext = 3.5f * hb * fabsf(ex) + 1.5f * hb * (fabsf(ey) + fabsf(ez)) + 1e-3f;
-                    const bool inner = fabsf(fmaf(cx, ex, fmaf(cy, ey, cz * ez))) + pext <= hl;
+                if (ci < n_c) {
+                    // the mask and the staging record are loaded together (one latency)
+                    const int64_t c = c_begin + ci;
+                    const uint32_t msk = P.c_mask[c];
+                    s0 = P.c_rec[3 * c + 0];
+                    s1 = P.c_rec[3 * c + 1];
+                    s2 = P.c_rec[3 * c + 2];
+                    keep = (msk >> sb) & 1u;
+                    // is the whole sub-brick between the transducer planes (|p| <= L / 2 at every
+                    // voxel centre)? p at its centre from the tile-origin base and the steps
+                    const float hx = s1.x, hy = s1.y, hz = s1.z;
+                    const float p0 = 0.5f * (s0.x + s0.y), hl = 0.5f * (s0.x - s0.y);
+                    const float pc = fmaf((float)(SXo + 3.5f), hx, fmaf((float)(SYo + 1.5f), hy, fmaf((float)(SZo + 1.5f), hz, p0)));
+                    const float pext = 3.5f * fabsf(hx) + 1.5f * (fabsf(hy) + fabsf(hz)) + 1e-3f;
+                    const bool inner = fabsf(pc) + pext <= hl;
                     // table base (a multiple of 8) with the inner / planar flags in bits 0, 1
-                    const uint32_t tb = (tab_addr + (uint32_t)(bnd * P.n_tab) * 8u - MAGIC_BITS_X8) |
-                                        (inner ? 1u : 0u) | (ez == 0.0f ? 2u : 0u);
-                    s0 = P.ebase[e];
-                    s1 = make_float4(hb * ex, hb * ey, hb * ez, P.ebase3[e]);
-                    s2 = make_float4(r.b.w, __uint_as_float(tb), __uint_as_float((uint32_t)d0),
-                                     __int_as_float((int)(d1 - d0)));
+                    const uint32_t bnd = (uint32_t)__float_as_int(s2.y);
+                    const uint32_t tb = (tab_addr + bnd * (uint32_t)P.n_tab * 8u - MAGIC_BITS_X8) | (inner ? 1u : 0u) |
+                                        (hz == 0.0f ? 2u : 0u);
+                    s2.y = __uint_as_float(tb);
                 }
                 const uint32_t bal = __ballot_sync(0xffffffffu, keep);
                 // ---- wait for this block's turn, then append its kept rows in lane order
@@ -819,23 +833,23 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
     P.out = out;
     P.V = g->V;
 
-    // compact candidate lists (rows with D entries and their sub-brick masks), then the units:
-    // the sub-bricks that some candidate of their tile may reach, heaviest tiles first
-    int32_t *c_ent = nullptr, *c_row = nullptr, *c_cnt = nullptr, *d_units = nullptr, *d_ctr = nullptr;
+    // compact candidate lists (rows with D entries, their staging records and sub-brick masks;
+    // 50 bytes per tile entry at most), then the units: the sub-bricks that some candidate of
+    // their tile may reach, heaviest tiles first
+    int32_t *c_cnt = nullptr, *d_units = nullptr, *d_ctr = nullptr;
+    float4* c_rec = nullptr;
     uint16_t *c_mask = nullptr, *c_or = nullptr;
     float2* tab_tc = nullptr;
     auto release = [&]() {
         cudaFree(tab_tc);
-        cudaFree(c_ent);
-        cudaFree(c_row);
+        cudaFree(c_rec);
         cudaFree(c_mask);
         cudaFree(c_cnt);
         cudaFree(c_or);
         cudaFree(d_units);
         cudaFree(d_ctr);
     };
-    cudaError_t e = cudaMalloc(&c_ent, sizeof(int32_t) * (size_t)g->E);
-    if (e == cudaSuccess) e = cudaMalloc(&c_row, sizeof(int32_t) * (size_t)g->E);
+    cudaError_t e = cudaMalloc(&c_rec, 3 * sizeof(float4) * (size_t)g->E);
     if (e == cudaSuccess) e = cudaMalloc(&c_mask, sizeof(uint16_t) * (size_t)g->E);
     if (e == cudaSuccess) e = cudaMalloc(&c_cnt, sizeof(int32_t) * (size_t)g->n_tiles);
     if (e == cudaSuccess) e = cudaMalloc(&c_or, sizeof(uint16_t) * (size_t)g->n_tiles);
@@ -853,8 +867,7 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx
         release();
         return cuda_fail(e, "psf tensor-core path: candidate lists");
     }
-    P.c_ent = c_ent;
-    P.c_row = c_row;
+    P.c_rec = c_rec;
     P.c_mask = c_mask;
     P.c_cnt = c_cnt;
     psf_mask_kernel<<<(unsigned)g->n_tiles, MASK_THREADS, 0, st>>>(P, c_or);

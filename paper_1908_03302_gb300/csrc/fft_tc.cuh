@@ -95,6 +95,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
+// The same test, letting the hardware suspend the thread for up to `ns` nanoseconds while the
+// phase is incomplete (a waiting warp then takes no issue slots from the working ones).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t mbar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // One arrival on the mbarrier (release semantics for this thread's prior shared-memory writes).
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile(
