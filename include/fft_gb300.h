@@ -156,7 +156,7 @@ typedef struct {
     int64_t evaluated_evals; /* (row, voxel) evaluations one apply performs after culling */
     int32_t phi_terms;       /* 0: sampled tables; else the largest sine-series length */
     double psf_tc_mma_flops; /* tensor-core MMA flops of the last fft_psf_batch call in mode 1:
-                                2 x 128 x 32 x N per chunk of generated J tile, N the MMA width */
+                                2 x 128 x 96 x N per chunk of generated J tile, N the MMA width */
 } fft_geom_info_t;
 fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info);
 
@@ -323,15 +323,19 @@ fft_status fft_cg_status(fft_geom g, void* stream);
  *   mode          0: FP32 CUDA cores, one PSF at a time: the column D = J_S e_k (one thread per
  *                    row of S), then a J^T that skips the rows where D is zero.
  *                 1: BF16 tensor cores: Y = J^T D for all n_subsets x n_spike columns of
- *                    D = J_S E at once. D is built as sparse rows (FP32 values); one persistent
- *                    kernel generates the J tile of each 8 x 4 x 4 voxel brick in FP32, rounds
- *                    it and D to BF16 and issues tcgen05.mma (K = 32 rows per step, up to 512
- *                    columns per launch; more columns run in blocks of spikes) accumulating
- *                    in FP32 in tensor memory. Relative L2 error ~1e-3 (BF16 operands); the cut
- *                    of a band whose Phi does not vanish at dt_max is taken in FP32 here (the
- *                    FP32 paths re-decide it in FP64). At most 32 subsets; a subset must not
- *                    list a row twice (FFT_ERR_ARG). FFT_ERR_TIMEOUT if a bounded wait on the
- *                    tensor cores gave up.
+ *                    D = J_S E at once. Rows are grouped by the set of subsets that hold them
+ *                    (nested subsets: one group per subset); D is built as sparse rows with one
+ *                    entry per (row, spike), and one persistent kernel generates the J tile of
+ *                    each 8 x 4 x 4 voxel brick in FP32, rounds it and D to BF16 and issues
+ *                    tcgen05.mma (96 rows of one group per chunk, N = the spikes of a launch)
+ *                    accumulating each group in FP32 in its own tensor-memory columns; each
+ *                    PSF is the sum of its subset's groups. Up to 144 spikes per launch with 3
+ *                    groups (more run in blocks of spikes); with more than 32 groups the
+ *                    subsets are taken one at a time. Relative L2 error ~1e-3 (BF16 operands);
+ *                    the cut of a band whose Phi does not vanish at dt_max is taken in FP32
+ *                    here (the FP32 paths re-decide it in FP64). At most 32 subsets; a subset
+ *                    must not list a row twice (FFT_ERR_ARG). FFT_ERR_TIMEOUT if a bounded wait
+ *                    on the tensor cores gave up.
  *                 2: FP32 CUDA cores, four columns per J^T: the columns of D taken in
  *                    (spike, subset) order, four at a time through the four-column J^T
  *                    (fft_JT_apply_batch), so that rows shared by a spike's nested subsets

@@ -187,9 +187,12 @@ int apply_occupancy(fft_geom g);
 size_t apply_smem(fft_geom g);
 void sharp_launch_shape(fft_geom g);
 void plain_launch_shape(fft_geom g);
-int psf_tc_max_cols(fft_geom g);
-fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint16_t* d_idx, const float* d_val, int n_rhs,
-                         const int32_t* col_map, float* out, cudaStream_t st);
+// Tensor-core PSFs: rows are grouped by the set of subsets that hold them (at most
+// PSF_TC_MAX_GROUPS distinct sets per launch).
+constexpr int PSF_TC_MAX_GROUPS = 32;
+int psf_tc_max_spikes(fft_geom g, int n_groups);
+fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent, const uint8_t* grp, int n_groups,
+                         const uint32_t* gmask, int n_sub, int n_spike, int k0, int nk, float* out, cudaStream_t st);
 int64_t ceil_div(int64_t a, int64_t b);
 // Resolve (and so load) the no-allocation PSF's static scratch on device `dev` (current).
 fft_status noalloc_prepare(int dev);

@@ -5,6 +5,7 @@
 // FP32 CUDA-core path: column k of J_S is evaluated row by row (one thread per row of S),
 // then J^T is applied to it. J^T skips rows whose weight is zero, so the cost of each PSF
 // follows the rows whose support holds the spike.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -49,12 +50,6 @@ __global__ void column_kernel(const RowRec* __restrict__ rec, const int32_t* __r
     D[p] = phi_lookup_global(vv, tab + (int64_t)b * n_tab, n_tab) * (is * ir) * r.b.w;
 }
 
-// mask[rows[i]] |= 1 << s: row membership of subset s.
-__global__ void subset_mask_kernel(const int32_t* __restrict__ rows, int n, int s, uint32_t* __restrict__ mask) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) atomicOr(&mask[rows[i]], 1u << s);
-}
-
 struct DParams {
     const RowRec* rec;
     const int32_t* row_band;
@@ -66,21 +61,21 @@ struct DParams {
     int nx, ny;
     const int64_t* spikes;    // spikes of this block
     int n_k;                  // spikes in the block
-    const uint32_t* mask;
+    const uint8_t* grp;       // group of each row (0xFF: in no subset)
     int64_t M;
     bool naive;
 };
 
-// Sparse rows of D for a block of spikes: entry (j = s * n_k + k, J[p, spike_k]) for every
-// subset s holding row p and every spike k with a non-zero entry. COUNT pass writes cnt[p],
-// FILL pass writes at off[p].
+// Sparse rows of D for a block of spikes, one entry per spike k with J[p, spike_k] != 0 for the
+// rows in some subset: k in bits 0-15 and the BF16 of C_p J[p, spike_k] in bits 16-31 (the
+// tensor-core kernel's B operand; its A tile holds J / C_p). COUNT pass writes cnt[p], FILL
+// pass writes at off[p].
 template <bool FILL>
 __global__ void dsparse_kernel(const DParams D, int32_t* __restrict__ cnt, const int64_t* __restrict__ off,
-                               uint16_t* __restrict__ idx, float* __restrict__ val) {
+                               uint32_t* __restrict__ ent) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= D.M) return;
-    const uint32_t mk = D.mask[p];
-    if (mk == 0) {
+    if (D.grp[p] == 0xFF) {
         if (!FILL) cnt[p] = 0;
         return;
     }
@@ -95,14 +90,10 @@ __global__ void dsparse_kernel(const DParams D, int32_t* __restrict__ cnt, const
         const float jv = jentry_f32(r, c, D.tab + (int64_t)b * D.n_tab, D.n_tab, D.rec64, (int)p, D.ox, D.oy, D.oz,
                                     D.h, ix, iy, iz, D.naive);
         if (jv == 0.0f) continue;
-        for (uint32_t m = mk; m; m &= m - 1) {
-            const int s = __ffs(m) - 1;
-            if (FILL) {
-                idx[o + n] = (uint16_t)(s * D.n_k + k);
-                val[o + n] = jv;
-            }
-            ++n;
-        }
+        if (FILL)
+            ent[o + n] = (uint32_t)k |
+                         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(jv * r.b.w)) << 16);
+        ++n;
     }
     if (!FILL) cnt[p] = n;
 }
@@ -115,42 +106,33 @@ using namespace fftgb;
 
 namespace {
 
-// Tensor-core path: spikes in blocks so that (subsets x spikes) <= 512 columns per launch.
-fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, const int32_t* subset_off,
-                       int32_t n_subsets, const int32_t* d_rows, float* out_dev, cudaStream_t st) {
-    const int max_cols = psf_tc_max_cols(g);
-    g->psf_tc_mma_flops = 0.0;
-    if (max_cols < n_subsets) {
+// Tensor-core path for subsets whose rows fall into at most PSF_TC_MAX_GROUPS groups (rows with
+// the same set of subsets holding them): D = J E for blocks of spikes, one launch per block.
+// out_dev is the output of subsets [0, n_subsets) with n_spike spikes each.
+fft_status psf_tc_groups(fft_geom g, const int64_t* spike_vox, int32_t n_spike, int32_t n_subsets,
+                         const std::vector<uint8_t>& grp, const std::vector<uint32_t>& gmask, float* out_dev,
+                         cudaStream_t st) {
+    const int n_groups = (int)gmask.size();
+    const int max_k = psf_tc_max_spikes(g, n_groups);
+    if (max_k < 1) {
         set_error("fft_psf_batch: the tensor-core tiles do not fit in shared memory with these tables");
         return FFT_ERR_ARG;
     }
-    const int k_blk = std::max(1, max_cols / n_subsets);
-    uint32_t* d_mask = nullptr;
+    const int k_blk = std::min<int>(max_k, n_spike);
+    uint8_t* d_grp = nullptr;
     int32_t* d_cnt = nullptr;
     int64_t* d_off = nullptr;
     int64_t* d_spk = nullptr;
-    int32_t* d_map = nullptr;
-    uint16_t* d_idx = nullptr;
-    float* d_val = nullptr;
+    uint32_t* d_ent = nullptr;
     fft_status rc = FFT_OK;
-    cudaError_t e = cudaMalloc(&d_mask, sizeof(uint32_t) * g->M);
+    cudaError_t e = cudaMalloc(&d_grp, g->M);
     if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int32_t) * g->M);
     if (e == cudaSuccess) e = cudaMalloc(&d_off, sizeof(int64_t) * (g->M + 1));
     if (e == cudaSuccess) e = cudaMalloc(&d_spk, sizeof(int64_t) * n_spike);
-    if (e == cudaSuccess) e = cudaMalloc(&d_map, sizeof(int32_t) * 512);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_mask, 0, sizeof(uint32_t) * g->M, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_grp, grp.data(), g->M, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_spk, spike_vox, sizeof(int64_t) * n_spike, cudaMemcpyHostToDevice, st);
-    for (int s = 0; s < n_subsets && e == cudaSuccess; ++s) {
-        const int n = subset_off[s + 1] - subset_off[s];
-        if (n > 0) {
-            subset_mask_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(d_rows + subset_off[s], n, s, d_mask);
-            e = cudaGetLastError();
-        }
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(out_dev, 0, sizeof(float) * (size_t)n_subsets * n_spike * g->V, st);
     std::vector<int32_t> cnt(g->M);
     std::vector<int64_t> off(g->M + 1);
-    std::vector<int32_t> cmap;
     for (int k0 = 0; k0 < n_spike && e == cudaSuccess && rc == FFT_OK; k0 += k_blk) {
         const int nk = std::min(k_blk, n_spike - k0);
         DParams D;
@@ -168,11 +150,11 @@ fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, co
         D.ny = g->grid.ny;
         D.spikes = d_spk + k0;
         D.n_k = nk;
-        D.mask = d_mask;
+        D.grp = d_grp;
         D.M = g->M;
         D.naive = (g->dt_mode == FFT_DT_NAIVE);
         const unsigned blocks = (unsigned)ceil_div(g->M, 128);
-        dsparse_kernel<false><<<blocks, 128, 0, st>>>(D, d_cnt, nullptr, nullptr, nullptr);
+        dsparse_kernel<false><<<blocks, 128, 0, st>>>(D, d_cnt, nullptr, nullptr);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * g->M, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -185,34 +167,65 @@ fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, co
             set_error("fft_psf_batch: more than 2^32 - 1 non-zeros in one block of D; use fewer spikes per call");
             break;
         }
-        cudaFree(d_idx);
-        cudaFree(d_val);
-        d_idx = nullptr;
-        d_val = nullptr;
-        e = cudaMalloc(&d_idx, sizeof(uint16_t) * (nnz > 0 ? nnz : 1));
-        if (e == cudaSuccess) e = cudaMalloc(&d_val, sizeof(float) * (nnz > 0 ? nnz : 1));
+        if (nnz == 0) continue;
+        cudaFree(d_ent);
+        d_ent = nullptr;
+        e = cudaMalloc(&d_ent, sizeof(uint32_t) * nnz);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * (g->M + 1), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && nnz > 0) {
-            dsparse_kernel<true><<<blocks, 128, 0, st>>>(D, nullptr, d_off, d_idx, d_val);
+        if (e == cudaSuccess) {
+            dsparse_kernel<true><<<blocks, 128, 0, st>>>(D, nullptr, d_off, d_ent);
             e = cudaGetLastError();
         }
-        // column (s * nk + k) of this block is output (s * n_spike + k0 + k)
-        cmap.assign((size_t)n_subsets * nk, 0);
-        for (int s = 0; s < n_subsets; ++s)
-            for (int k = 0; k < nk; ++k) cmap[(size_t)s * nk + k] = s * n_spike + k0 + k;
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_map, cmap.data(), sizeof(int32_t) * cmap.size(), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess && nnz > 0) rc = launch_psf_tc(g, d_off, d_idx, d_val, n_subsets * nk, d_map, out_dev, st);
+        if (e == cudaSuccess)
+            rc = launch_psf_tc(g, d_off, d_ent, d_grp, n_groups, gmask.data(), n_subsets, n_spike, k0, nk, out_dev, st);
     }
-    cudaFree(d_mask);
+    cudaFree(d_grp);
     cudaFree(d_cnt);
     cudaFree(d_off);
     cudaFree(d_spk);
-    cudaFree(d_map);
-    cudaFree(d_idx);
-    cudaFree(d_val);
+    cudaFree(d_ent);
     if (rc != FFT_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "fft_psf_batch (tensor cores)");
+    return FFT_OK;
+}
+
+// Tensor-core path. Rows are grouped by the set of subsets that hold them (for nested subsets
+// one group per subset); with more than PSF_TC_MAX_GROUPS distinct sets the subsets are taken
+// one at a time.
+fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, const int32_t* subset_off,
+                       int32_t n_subsets, const int32_t* subset_rows, float* out_dev, cudaStream_t st) {
+    g->psf_tc_mma_flops = 0.0;
+    cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(float) * (size_t)n_subsets * n_spike * g->V, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fft_psf_batch (tensor cores)");
+    std::vector<uint32_t> member(g->M, 0u);
+    for (int s = 0; s < n_subsets; ++s)
+        for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) member[subset_rows[i]] |= 1u << s;
+    std::vector<uint32_t> gmask;   // distinct non-empty sets, in order of first appearance
+    std::vector<uint8_t> grp(g->M, 0xFF);
+    bool fits = true;
+    for (int64_t p = 0; p < g->M && fits; ++p) {
+        if (!member[p]) continue;
+        size_t gi = 0;
+        while (gi < gmask.size() && gmask[gi] != member[p]) ++gi;
+        if (gi == gmask.size()) {
+            if ((int)gmask.size() == PSF_TC_MAX_GROUPS) {
+                fits = false;
+                break;
+            }
+            gmask.push_back(member[p]);
+        }
+        grp[p] = (uint8_t)gi;
+    }
+    if (gmask.empty()) return FFT_OK;
+    if (fits) return psf_tc_groups(g, spike_vox, n_spike, n_subsets, grp, gmask, out_dev, st);
+    for (int s = 0; s < n_subsets; ++s) {
+        std::fill(grp.begin(), grp.end(), (uint8_t)0xFF);
+        for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) grp[subset_rows[i]] = 0;
+        if (subset_off[s + 1] == subset_off[s]) continue;
+        const std::vector<uint32_t> one(1, 1u);
+        fft_status rc = psf_tc_groups(g, spike_vox, n_spike, 1, grp, one, out_dev + (int64_t)s * n_spike * g->V, st);
+        if (rc != FFT_OK) return rc;
+    }
     return FFT_OK;
 }
 
@@ -302,7 +315,7 @@ extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_
     cudaError_t e = cudaSuccess;
     if (n_idx > 0) e = cudaMemcpyAsync(d_rows, subset_rows, sizeof(int32_t) * n_idx, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && mode == 1) {
-        rc = psf_tc_path(g, spike_vox, n_spike, subset_off, n_subsets, d_rows, out_dev, st);
+        rc = psf_tc_path(g, spike_vox, n_spike, subset_off, n_subsets, subset_rows, out_dev, st);
         cudaError_t e2 = cudaStreamSynchronize(st);
         cudaFree(d_rows);
         if (rc != FFT_OK) return rc;

@@ -1,7 +1,9 @@
 """Batched Hessian PSFs on the tensor cores (BF16 operands, FP32 accumulation in TMEM)
-against the FP64 oracle (relative L2 <= 1e-2 per PSF) and against the FP32 CUDA-core path,
-including more than 256 right-hand sides (two MMAs per K step) and more than 512 (spike
-blocks)."""
+against the FP64 oracle (relative L2 <= 1e-2 per PSF) and against the FP32 CUDA-core path:
+nested ring subsets (one row group per subset, PSFs as prefix sums of the groups), overlapping
+subsets that are not nested (a row group per combination of subsets), more subset
+combinations than one launch takes (subsets one at a time), and more spikes than one launch
+takes (spike blocks)."""
 import numpy as np
 import pytest
 
@@ -46,8 +48,8 @@ def test_psf_tc_matches_oracle(ring32):
 
 @pytest.mark.parametrize("n_spike", [100, 200])
 def test_psf_tc_many_rhs(ring32, n_spike):
-    # 3 subsets x 100 spikes = 300 columns (two MMAs per K step);
-    # 3 x 200 = 600 columns (spike blocks of 170)
+    # 3 nested subsets x 100 spikes: one launch (3 row groups x 112 accumulator columns);
+    # 3 x 200: two spike blocks
     w, og, geo = ring32
     spikes = wl.random_voxels(w.grid, n_spike, 9, rho_max=0.04, z_max=0.014)
     subsets = ring_subsets32(og.M)
@@ -92,3 +94,38 @@ def test_psf_tc_transducer_on_a_voxel_centre():
         for k in range(3):
             assert rel_l2(fp[s, k], ref[s, k]) <= 1e-5
             assert rel_l2(tc[s, k], ref[s, k]) <= 1e-2
+
+
+def test_psf_tc_overlapping_subsets(ring32):
+    # two overlapping subsets, neither inside the other: rows of the first only, of the second
+    # only and of both form three groups; each PSF sums the two groups of its subset
+    w, og, geo = ring32
+    local = wl.unordered_pairs(range(32))
+    even = np.flatnonzero((local[:, 0] % 2 == 0) & (local[:, 1] % 2 == 0)).astype(np.int32)
+    low = np.flatnonzero(local[:, 1] < 20).astype(np.int32)
+    assert 0 < len(np.intersect1d(even, low)) < min(len(even), len(low))
+    spikes = wl.random_voxels(w.grid, 5, 21, rho_max=0.035, z_max=0.012)
+    subsets = [even, low]
+    ref = og.psf(spikes, subsets)
+    tc = to_np(geo.psf_batch(spikes, subsets, mode=1))
+    for s in range(2):
+        for k in range(len(spikes)):
+            assert rel_l2(tc[s, k], ref[s, k]) <= 1e-2
+
+
+def test_psf_tc_many_subset_combinations(ring32):
+    # six random halves of the rows: up to 63 distinct combinations, more than one launch
+    # groups, so the subsets are taken one at a time
+    w, og, geo = ring32
+    rng = np.random.default_rng(22)
+    subsets = [np.flatnonzero(rng.random(og.M) < 0.5).astype(np.int32) for _ in range(6)]
+    member = np.zeros(og.M, dtype=np.int64)
+    for s, rows in enumerate(subsets):
+        member[rows] |= 1 << s
+    assert len(np.unique(member[member > 0])) > 32
+    spikes = wl.random_voxels(w.grid, 4, 23, rho_max=0.035, z_max=0.012)
+    tc = to_np(geo.psf_batch(spikes, subsets, mode=1))
+    fp = to_np(geo.psf_batch(spikes, subsets, mode=0))
+    for s in range(len(subsets)):
+        for k in range(len(spikes)):
+            assert rel_l2(tc[s, k], fp[s, k]) <= 1e-2
