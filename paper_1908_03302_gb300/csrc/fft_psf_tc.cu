@@ -14,11 +14,11 @@
 // (for nested subsets: prefix sums).
 //
 // One persistent CTA per SM runs a pipeline of three warp roles over units (tile, sub-brick):
-//   * 2 scan warps stream the tile's compact candidate lists (built once per call by
+//   * 3 scan warps stream the tile's compact candidate lists (built once per call by
 //     psf_mask_kernel, one segment per group: the tile's rows that have D entries, each with a
 //     16-bit mask of the sub-bricks its support may reach and its staging record), keep the
 //     rows whose mask holds the unit's sub-brick, 32 candidates per warp and block, and append
-//     their records to a ring of 4 chunks of 96 rows in shared memory, groups in order and
+//     their records to a ring of 6 chunks of 96 rows in shared memory, groups in order and
 //     candidates in order within a group (the blocks take turns), so the K order is fixed.
 //     A chunk holds the rows of one group; it is published with a header (unit, rows, group,
 //     first of the unit / of its group in the unit, last of the unit) on its "ring full"
@@ -35,7 +35,7 @@
 //     commits to the stage's "done" mbarrier; one chunk later it waits for those MMAs and
 //     zero-fills the stage's B tile with one bulk asynchronous copy from a zero page, which
 //     completes the stage's "empty" mbarrier that the generators wait for before reusing it.
-// Three A / B stages and the 4-chunk row ring decouple the roles: no CTA-wide barrier between
+// Three A / B stages and the 6-chunk row ring decouple the roles: no CTA-wide barrier between
 // the first and the last unit. The Phi tables are held in shared memory; where the geometry's
 // tables and the stages do not fit together, the kernel takes the tables at half resolution
 // (resampled from the device tables by the linear interpolant; the extra interpolation error,
@@ -62,18 +62,19 @@ constexpr int KC = 96;                 // rows per chunk (MMA K per chunk)
 constexpr int GEN_WARPS = 24;          // warps that generate J and scatter D (warps 0 ..)
 constexpr int ROW_OCTETS = KC / 8;     // generator warp w: rows 8 (w % 12) .., voxel half w / 12
 constexpr int D_ROWS = KC / GEN_WARPS; // rows whose D entries a generator warp scatters
-constexpr int SCAN_WARPS = 2;          // warps that scan candidate rows (warps 24, 25)
+constexpr int SCAN_WARPS = 3;          // warps that scan candidate rows (warps 24 .. 26)
 constexpr int MMA_WARP = GEN_WARPS + SCAN_WARPS;   // the warp that issues the MMAs
 constexpr int TC_WARPS = MMA_WARP + 1;
 constexpr int TC_THREADS = TC_WARPS * 32;
 constexpr int NSTAGE = 3;              // A / B stages
-constexpr int RING = 4;                // chunks of staged rows between the scan and the generation
+constexpr int RING = 6;                // chunks of staged rows between the scan and the generation
 constexpr int D_LANES = 16;            // lanes that scatter one row's D entries
 constexpr long long WAIT_BUDGET = 4000000000ll;   // cycles (~2 s)
 constexpr int HDR_UFIRST = 1, HDR_LAST = 2, HDR_GFIRST = 4;   // chunk header flags
 constexpr int MAX_NG = 256;            // MMA N (spikes of one launch, rounded up to 16)
-// Stand-in for a row past a chunk's end: a voxel line at distance FAR from the pair's axis
-// (in band units), so that every detour form gives v = 2 FAR, saturated to the cut-off: Phi = 0.
+// Stand-in for a row past a chunk's end: a voxel line at distance FAR from the pair's axis and
+// at its midplane (in band units), so that every detour form gives v = 2 FAR, saturated to the
+// cut-off: Phi = 0, and the geometric factor stays finite.
 constexpr float FAR = 1.0e4f;
 static_assert(GEN_WARPS == 2 * ROW_OCTETS && D_ROWS == 4, "generator warps: 8 rows x 64 voxels");
 
@@ -172,9 +173,20 @@ __device__ __forceinline__ bool warp_wait(uint32_t mbar, uint32_t parity, int32_
 }
 
 // Producer side, called by the scan warp that holds the turn (whole warp): publish chunk
-// `chunk` (lane 0 writes the header and arrives on its "ring full" barrier).
-__device__ __forceinline__ void publish_chunk(TcShared& S, uint32_t ring_full0, int chunk, int unit, int n_rows,
-                                              int flags, int group, int lane) {
+// `chunk` (lane 0 writes the header and arrives on its "ring full" barrier). The rows past
+// n_rows get the stand-in record (a voxel line FAR from the pair's axis, no D entries, table
+// base `tb_safe` with both detour-form flags), so that the generators load every row of a
+// chunk alike and the stand-ins contribute exact zeros.
+__device__ __forceinline__ void publish_chunk(TcShared& S, float4* s_ring, uint32_t ring_full0, int chunk, int unit,
+                                              int n_rows, int flags, int group, uint32_t tb_safe, int lane) {
+    if (n_rows >= 0) {
+        float4* dst = s_ring + (size_t)(chunk % RING) * KC * 3;
+        for (int r = n_rows + lane; r < KC; r += 32) {
+            dst[3 * r + 0] = make_float4(0.f, 0.f, FAR, 0.f);
+            dst[3 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            dst[3 * r + 2] = make_float4(0.f, __uint_as_float(tb_safe), 0.f, 0.f);
+        }
+    }
     __threadfence_block();
     __syncwarp();
     if (lane == 0) {
@@ -321,6 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         for (uint32_t i = tid; i < NSTAGE * b_bytes / 16; i += TC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
     }
     const uint32_t tab_addr = smem_addr(s_tab);
+    const uint32_t tb_safe = (tab_addr - MAGIC_BITS_X8) | 3u;   // band 0, both detour-form flags
     const float nm1 = (float)(P.n_tab - 1);
     const uint32_t full0 = smem_addr(&S.full[0]), empty0 = smem_addr(&S.empty[0]), done0 = smem_addr(&S.done[0]);
     const uint32_t ring_full0 = smem_addr(&S.ring_full[0]), ring_empty0 = smem_addr(&S.ring_empty[0]);
@@ -373,8 +386,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                         // a unit whose rows filled its last chunk exactly gets an empty closing chunk
                         if (pf == 0) failed = failed || !ring_slot_free(ring_empty0, pc, P.status);
                         if (!failed)
-                            publish_chunk(S, ring_full0, pc, P.units[S.scan_unit], pf, HDR_LAST | S.p_flags,
-                                          S.p_group, lane);
+                            publish_chunk(S, s_ring, ring_full0, pc, P.units[S.scan_unit], pf,
+                                          HDR_LAST | S.p_flags, S.p_group, tb_safe, lane);
                         __syncwarp();
                         if (lane == 0) {
                             S.p_chunk = pc + 1;
@@ -475,7 +488,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                     int pc = S.p_chunk, pf = S.p_fill, fl = S.p_flags, cg = S.p_group;
                     if (cg != g) {   // a chunk holds one group: close the other group's chunk
                         if (pf > 0) {
-                            publish_chunk(S, ring_full0, pc, ucode, pf, fl, cg, lane);
+                            publish_chunk(S, s_ring, ring_full0, pc, ucode, pf, fl, cg, tb_safe, lane);
                             ++pc;
                             pf = 0;
                             fl &= ~HDR_UFIRST;
@@ -498,7 +511,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                     }
                     int nf = pf + n;
                     if (nf >= KC) {   // the chunk is full: publish it
-                        publish_chunk(S, ring_full0, pc, ucode, KC, fl, cg, lane);
+                        publish_chunk(S, s_ring, ring_full0, pc, ucode, KC, fl, cg, tb_safe, lane);
                         ++pc;
                         nf -= KC;
                         fl = 0;
@@ -521,7 +534,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         }
         if (k == 0 && !failed) {   // no more units: tell the consumers
             const int pc = S.p_chunk;
-            if (ring_slot_free(ring_empty0, pc, P.status)) publish_chunk(S, ring_full0, pc, 0, -1, 0, 0, lane);
+            if (ring_slot_free(ring_empty0, pc, P.status))
+                publish_chunk(S, s_ring, ring_full0, pc, 0, -1, 0, 0, tb_safe, lane);
         }
     } else if (warp < GEN_WARPS) {
         // ================= generator warps
@@ -540,7 +554,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
         // byte offset of (MMA row 64 hv + g, K pair ra) in a stage; voxel t adds t x 16 KC
         const uint32_t a_off0 = tc::kmajor_offset((uint32_t)(64 * hv + gg), (uint32_t)ra, KC);
         const float Yv0 = (float)(gg & 3), Zv0 = (float)(2 * hv + (gg >> 2));
-        const uint32_t tb_safe = (tab_addr - MAGIC_BITS_X8) | 3u;
         uint32_t upres = 0u;   // groups with chunks in the current unit
         for (;; ++chunk) {
             const int slot = chunk % RING;
@@ -550,7 +563,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
             }
             const ChunkHdr h = S.hdr[slot];
             if (h.n_rows < 0) break;
-            const int nrows = h.n_rows;
             upres |= 1u << h.group;
             const int T = h.unit >> 4, sb = h.unit & 15;
             const int SX = 8 * (sb & 1), SY = 4 * ((sb >> 1) & 3), SZ = 4 * (sb >> 3);
@@ -566,13 +578,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
 #pragma unroll
             for (int dp = 0; dp < 2; ++dp) {
                 const int dr = D_ROWS * warp + 2 * dp + (lane >> 4);
-                d_beg[dp] = 0;
-                d_cnt[dp] = 0;
-                if (dr < nrows) {
-                    const float4 C = stg[dr * 3 + 2];
-                    d_beg[dp] = __float_as_uint(C.z);
-                    d_cnt[dp] = __float_as_int(C.w);
-                }
+                const float4 C = stg[dr * 3 + 2];   // a stand-in row has no D entries
+                d_beg[dp] = __float_as_uint(C.z);
+                d_cnt[dp] = __float_as_int(C.w);
                 e0[dp] = d_i0 < d_cnt[dp] ? P.d_ent[d_beg[dp] + d_i0] : 0u;
                 e1[dp] = d_i0 + D_LANES < d_cnt[dp] ? P.d_ent[d_beg[dp] + d_i0 + D_LANES] : 0u;
             }
@@ -581,17 +589,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                 failed = true;
                 break;
             }
-            // generate A: this lane's rows ra, ra + 1 on its eight voxels. A row past the chunk's
-            // end is replaced by a stand-in far outside every support (Phi = 0 exactly). The
-            // detour form is chosen per warp: the inner / planar forms only where all its rows
-            // allow them.
-            const bool va = ra < nrows, vb = ra + 1 < nrows;
-            const float4 Aa = va ? stg[ra * 3 + 0] : make_float4(0.f, 0.f, FAR, 0.f);
-            const float4 Ba = va ? stg[ra * 3 + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const uint32_t ta = va ? __float_as_uint(stg[ra * 3 + 2].y) : tb_safe;
-            const float4 Ab = vb ? stg[ra * 3 + 3] : make_float4(0.f, 0.f, FAR, 0.f);
-            const float4 Bb = vb ? stg[ra * 3 + 4] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const uint32_t tbb = vb ? __float_as_uint(stg[ra * 3 + 5].y) : tb_safe;
+            // generate A: this lane's rows ra, ra + 1 on its eight voxels (a row past the chunk's
+            // end is the producer's stand-in: Phi = 0 exactly). The detour form is chosen per
+            // warp: the inner / planar forms only where all its rows allow them.
+            const float4 Aa = stg[ra * 3 + 0], Ba = stg[ra * 3 + 1];
+            const uint32_t ta = __float_as_uint(stg[ra * 3 + 2].y);
+            const float4 Ab = stg[ra * 3 + 3], Bb = stg[ra * 3 + 4];
+            const uint32_t tbb = __float_as_uint(stg[ra * 3 + 5].y);
             const uint32_t fl = ta & tbb & 3u;
             const uint32_t wfl = (__all_sync(0xffffffffu, fl & 1u) ? 1u : 0u) | (__all_sync(0xffffffffu, fl & 2u) ? 2u : 0u);
             const float Xv = (float)SX, Yv = (float)SY + Yv0, Zv = (float)SZ + Zv0;
