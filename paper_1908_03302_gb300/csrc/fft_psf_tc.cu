@@ -15,8 +15,8 @@
 //
 // One persistent CTA per SM runs a pipeline of three warp roles over units (tile, sub-brick):
 //   * 3 scan warps stream the tile's compact candidate lists (built once per call by
-//     psf_mask_kernel, one segment per group: the tile's rows that have D entries, each with a
-//     16-bit mask of the sub-bricks its support may reach and its staging record), keep the
+//     psf_mask_kernel, one segment per group: the tile's rows that have D entries, each with its
+//     staging record and the 16-bit mask of the sub-bricks its support may reach), keep the
 //     rows whose mask holds the unit's sub-brick, 32 candidates per warp and block, and append
 //     their records to a ring of 6 chunks of 96 rows in shared memory, groups in order and
 //     candidates in order within a group (the blocks take turns), so the K order is fixed.
@@ -94,8 +94,7 @@ struct PsfTcParams {
     const uint8_t* grp;        // group of each row (0xFF: the row is in no subset)
     int n_groups;              // G (<= PSF_TC_MAX_GROUPS)
     const int64_t* seg_off;    // [n_tiles * G] first compact candidate of (tile, group)
-    float4* c_rec;             // compact candidates: staging record (3 float4, see psf_mask_kernel),
-    uint16_t* c_mask;          //   sub-bricks the row may reach
+    float4* c_rec;             // compact candidates: staging record (3 float4, see psf_mask_kernel)
     int32_t* c_cnt;            // [n_tiles * G] compact candidates of (tile, group)
     const int32_t* units;      // (tile << 4) | sub-brick, heaviest tiles first
     int n_units;
@@ -233,7 +232,8 @@ __global__ void __launch_bounds__(MASK_THREADS) psf_cap_kernel(const PsfTcParams
 // offsets:
 //   r0 = the entry's tile-origin base (p + L/2, p - L/2, c1, c2) in the pair frame,
 //   r1 = (h e_x, h e_y, h e_z, c3) (pair-frame steps per voxel and the base's c3),
-//   r2 = (0, band index, first D entry of the row, D entries of the row) (bits).
+//   r2 = (mask of the sub-bricks, band index, first D entry of the row, D entries of the row)
+//        (bits).
 __global__ void __launch_bounds__(MASK_THREADS) psf_mask_kernel(const PsfTcParams P, uint16_t* __restrict__ c_or) {
     __shared__ int wsum[PSF_TC_MAX_GROUPS][MASK_THREADS / 32];
     __shared__ int64_t run[PSF_TC_MAX_GROUPS];
@@ -292,8 +292,8 @@ __global__ void __launch_bounds__(MASK_THREADS) psf_mask_kernel(const PsfTcParam
             const int64_t pos = P.seg_off[(int64_t)T * G + mg] + run[mg] + before + rank;
             P.c_rec[3 * pos + 0] = r0;
             P.c_rec[3 * pos + 1] = r1;
+            r2.x = __uint_as_float(mask);
             P.c_rec[3 * pos + 2] = r2;
-            P.c_mask[pos] = (uint16_t)mask;
         }
         __syncthreads();
         if (threadIdx.x < G) {
@@ -435,23 +435,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) psf_tc_kernel(const __grid_cons
                 if (lane >= o) g_end += x;
             }
             const int n_blocks = __shfl_sync(0xffffffffu, g_end, 31);
-            for (int b = k; b < n_blocks && !failed; b += SCAN_WARPS) {
-                // ---- block b: group g, its block bl; keep the candidates that reach the sub-brick
+            // the gathers of block b (its group g, its block bl within the group): the staging
+            // record of each lane's candidate (its sub-brick mask in r2.x), zero past the group's end
+            auto gather = [&](int b, float4& r0, float4& r1, float4& r2) {
+                r0 = r1 = r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (b >= n_blocks) return;
                 const int g = __popc(__ballot_sync(0xffffffffu, g_end <= b));
                 const int bl = b - (__shfl_sync(0xffffffffu, g_end, g) - __shfl_sync(0xffffffffu, g_nb, g));
                 const int n_c = __shfl_sync(0xffffffffu, g_cnt, g);
                 const long long seg = __shfl_sync(0xffffffffu, g_seg, g);
                 const int ci = 32 * bl + lane;
-                bool keep = false;
-                float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
                 if (ci < n_c) {
-                    // the mask and the staging record are loaded together (one latency)
                     const int64_t c = seg + ci;
-                    const uint32_t msk = P.c_mask[c];
-                    s0 = P.c_rec[3 * c + 0];
-                    s1 = P.c_rec[3 * c + 1];
-                    s2 = P.c_rec[3 * c + 2];
-                    keep = (msk >> sb) & 1u;
+                    r0 = P.c_rec[3 * c + 0];
+                    r1 = P.c_rec[3 * c + 1];
+                    r2 = P.c_rec[3 * c + 2];
+                }
+            };
+            for (int b = k; b < n_blocks && !failed; b += SCAN_WARPS) {
+                float4 s0, s1, s2;
+                gather(b, s0, s1, s2);
+                const int g = __popc(__ballot_sync(0xffffffffu, g_end <= b));
+                // ---- block b: keep the candidates that reach the sub-brick
+                const bool keep = (__float_as_uint(s2.x) >> sb) & 1u;
+                if (keep) {
                     // is the whole sub-brick between the transducer planes (|p| <= L / 2 at every
                     // voxel centre)? p at its centre from the tile-origin base and the steps
                     const float hx = s1.x, hy = s1.y, hz = s1.z;
@@ -899,20 +906,19 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent
     P.out = out;
     P.V = g->V;
 
-    // compact candidate lists by group (rows with D entries, their staging records and
-    // sub-brick masks; 50 bytes per tile entry at most): segment capacities first, then the
+    // compact candidate lists by group (rows with D entries and their staging records, which
+    // hold the sub-brick masks; 48 bytes per tile entry at most): segment capacities first, then the
     // lists, then the units: the sub-bricks that some candidate of their tile may reach,
     // heaviest tiles first
     const int64_t n_seg = g->n_tiles * n_groups;
     int32_t *c_cnt = nullptr, *d_units = nullptr, *d_ctr = nullptr, *d_cap = nullptr;
     int64_t* d_seg = nullptr;
     float4* c_rec = nullptr;
-    uint16_t *c_mask = nullptr, *c_or = nullptr;
+    uint16_t* c_or = nullptr;
     float2* tab_tc = nullptr;
     auto release = [&]() {
         cudaFree(tab_tc);
         cudaFree(c_rec);
-        cudaFree(c_mask);
         cudaFree(c_cnt);
         cudaFree(c_or);
         cudaFree(d_units);
@@ -952,7 +958,6 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent
         return FFT_OK;
     }
     if (e == cudaSuccess) e = cudaMalloc(&c_rec, 3 * sizeof(float4) * (size_t)n_cand);
-    if (e == cudaSuccess) e = cudaMalloc(&c_mask, sizeof(uint16_t) * (size_t)n_cand);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_seg, seg.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
         release();
@@ -960,7 +965,6 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent
     }
     P.seg_off = d_seg;
     P.c_rec = c_rec;
-    P.c_mask = c_mask;
     P.c_cnt = c_cnt;
     psf_mask_kernel<<<(unsigned)g->n_tiles, MASK_THREADS, 0, st>>>(P, c_or);
     e = cudaGetLastError();
