@@ -129,3 +129,38 @@ def test_psf_tc_many_subset_combinations(ring32):
     for s in range(len(subsets)):
         for k in range(len(spikes)):
             assert rel_l2(tc[s, k], fp[s, k]) <= 1e-2
+
+
+def test_psf_tc_many_nested_groups(ring32):
+    # eight nested subsets (rows whose two elements lie in the first 4, 8, ..., 32 elements of
+    # a seeded order): eight row groups of at most 64 accumulator columns each (512 / 8), so
+    # 100 spikes run in two launches (64 + 36), and each PSF sums up to eight groups
+    w, og, geo = ring32
+    local = wl.unordered_pairs(range(32))
+    order = np.random.default_rng(24).permutation(32)
+    rank = np.empty(32, dtype=np.int64)
+    rank[order] = np.arange(32)
+    top = np.maximum(rank[local[:, 0]], rank[local[:, 1]])
+    subsets = [np.flatnonzero(top < n).astype(np.int32) for n in range(4, 33, 4)]
+    spikes = wl.random_voxels(w.grid, 100, 25, rho_max=0.035, z_max=0.012)
+    tc = to_np(geo.psf_batch(spikes, subsets, mode=1))
+    fp = to_np(geo.psf_batch(spikes, subsets, mode=0))
+    checked = 0
+    for s in range(len(subsets)):
+        for k in range(len(spikes)):
+            if np.linalg.norm(fp[s, k]) > 0:
+                assert rel_l2(tc[s, k], fp[s, k]) <= 1e-2
+                checked += 1
+    assert checked > len(spikes)
+
+
+def test_psf_tc_bitwise_repeatable(ring32):
+    # the K order of every MMA chain is fixed (groups in order, candidates in order), so two
+    # calls give the same bits
+    w, og, geo = ring32
+    spikes = wl.random_voxels(w.grid, 24, 26, rho_max=0.035, z_max=0.012)
+    subsets = ring_subsets32(og.M)
+    a = geo.psf_batch(spikes, subsets, mode=1).cpu().numpy()
+    b = geo.psf_batch(spikes, subsets, mode=1).cpu().numpy()
+    assert np.linalg.norm(a) > 0
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
