@@ -194,12 +194,15 @@ fft_status psf_tc_groups(fft_geom g, const int64_t* spike_vox, int32_t n_spike, 
 // one at a time.
 fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, const int32_t* subset_off,
                        int32_t n_subsets, const int32_t* subset_rows, float* out_dev, cudaStream_t st) {
+    std::vector<uint32_t> member(g->M, 0u);
+    for (int s = 0; s < n_subsets; ++s)
+        for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) {
+            FFT_ARG(!((member[subset_rows[i]] >> s) & 1u), "fft_psf_batch: a subset lists a row twice");
+            member[subset_rows[i]] |= 1u << s;
+        }
     g->psf_tc_mma_flops = 0.0;
     cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(float) * (size_t)n_subsets * n_spike * g->V, st);
     if (e != cudaSuccess) return cuda_fail(e, "fft_psf_batch (tensor cores)");
-    std::vector<uint32_t> member(g->M, 0u);
-    for (int s = 0; s < n_subsets; ++s)
-        for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) member[subset_rows[i]] |= 1u << s;
     std::vector<uint32_t> gmask;   // distinct non-empty sets, in order of first appearance
     std::vector<uint8_t> grp(g->M, 0xFF);
     bool fits = true;
@@ -298,30 +301,18 @@ extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_
     FFT_ARG(n_idx == 0 || subset_rows, "fft_psf_batch: null subset_rows");
     for (int32_t i = 0; i < n_idx; ++i)
         FFT_ARG(subset_rows[i] >= 0 && subset_rows[i] < g->M, "fft_psf_batch: subset row out of range");
-    if (mode == 1) {
-        std::vector<uint8_t> seen;
-        for (int s = 0; s < n_subsets; ++s) {
-            seen.assign(g->M, 0);
-            for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) {
-                FFT_ARG(!seen[subset_rows[i]], "fft_psf_batch: a subset lists a row twice");
-                seen[subset_rows[i]] = 1;
-            }
-        }
-    }
-
     cudaStream_t st = (cudaStream_t)stream;
-    int32_t* d_rows = nullptr;
-    FFT_CUDA(cudaMalloc(&d_rows, sizeof(int32_t) * (n_idx > 0 ? n_idx : 1)));
-    cudaError_t e = cudaSuccess;
-    if (n_idx > 0) e = cudaMemcpyAsync(d_rows, subset_rows, sizeof(int32_t) * n_idx, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && mode == 1) {
+    if (mode == 1) {   // (rows listed twice in a subset are rejected there, before any device work)
         rc = psf_tc_path(g, spike_vox, n_spike, subset_off, n_subsets, subset_rows, out_dev, st);
         cudaError_t e2 = cudaStreamSynchronize(st);
-        cudaFree(d_rows);
         if (rc != FFT_OK) return rc;
         if (e2 != cudaSuccess) return cuda_fail(e2, "fft_psf_batch sync");
         return FFT_OK;
     }
+    int32_t* d_rows = nullptr;
+    FFT_CUDA(cudaMalloc(&d_rows, sizeof(int32_t) * (n_idx > 0 ? n_idx : 1)));
+    cudaError_t e = cudaSuccess;
+    if (n_idx > 0) e = cudaMemcpyAsync(d_rows, subset_rows, sizeof(int32_t) * n_idx, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && mode == 2) {
         rc = psf_fp32_batched(g, spike_vox, n_spike, subset_off, n_subsets, d_rows, out_dev, st);
         cudaError_t e2 = cudaStreamSynchronize(st);

@@ -164,3 +164,14 @@ def test_psf_tc_bitwise_repeatable(ring32):
     b = geo.psf_batch(spikes, subsets, mode=1).cpu().numpy()
     assert np.linalg.norm(a) > 0
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def test_psf_tc_rejects_a_row_listed_twice(ring32):
+    import paper_1908_03302_gb300 as fg
+    w, og, geo = ring32
+    rows = np.arange(0, og.M, 3, dtype=np.int32)
+    bad = np.sort(np.concatenate([rows, rows[5:6]])).astype(np.int32)
+    spikes = wl.random_voxels(w.grid, 2, 27, rho_max=0.035, z_max=0.012)
+    with pytest.raises(fg.FFTError) as ei:
+        geo.psf_batch(spikes, [rows, bad], mode=1)
+    assert ei.value.status == fg._lib.FFT_ERR_ARG
