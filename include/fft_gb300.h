@@ -313,6 +313,40 @@ fft_status fft_cg_solve(fft_geom g, const float* d_dev, double lambda_rel, int32
 fft_status fft_cg_status(fft_geom g, void* stream);
 
 /*
+ * fft_cg_continue - n_iter more CGLS iterations (Sec. II-D, Eq. leastSquare_misfit, as in
+ * fft_cg_solve) from the state the handle holds (left by the last fft_cg_solve,
+ * fft_cg_continue or fft_cg_load on it): the same loop as fft_cg_solve's,
+ * so a solve of k iterations continued for n gives the same bits as one solve of k + n.
+ *   m_dev     device float32[V], out: the model after the iterations (the state itself stays
+ *             in the handle; m_dev is not read).
+ *   hist_host nullable host double[n_iter + 1]: |J^T r - lambda m|^2 before the first of these
+ *             iterations and after each.
+ * Asynchronous and synchronising exactly like fft_cg_solve (a breakdown flag carried in the
+ * state stays set: its iterations keep m). FFT_ERR_STATE if the handle holds no CG state.
+ */
+fft_status fft_cg_continue(fft_geom g, int32_t n_iter, float* m_dev, double* hist_host, void* stream);
+
+/*
+ * Checkpoint and resume of a solve (plumbing around the CGLS of Sec. II-D; the paper has no
+ * counterpart). The state is (m, p, r, gamma, lambda, breakdown flag,
+ * iterations done), stored in FP32 / FP64 exactly as the loop keeps it, so a state saved,
+ * loaded into a handle of the same geometry and continued gives the same bits as the
+ * uninterrupted solve.
+ *   fft_cg_state_bytes  *bytes = size of a saved state: a 64-byte header, then m (V floats),
+ *                       p (V floats) and r (M floats).
+ *   fft_cg_save         copies the handle's state into host_buf (host memory, `bytes` >=
+ *                       fft_cg_state_bytes); synchronises `stream`. FFT_ERR_STATE if the
+ *                       handle holds no state, FFT_ERR_ARG if the buffer is too small.
+ *   fft_cg_load         replaces the handle's state by the one in host_buf (allocating the CG
+ *                       workspace on first use); synchronises `stream`. FFT_ERR_ARG if the
+ *                       buffer is not a state of fft_cg_save, is short, or was saved for
+ *                       another number of rows or voxels.
+ */
+fft_status fft_cg_state_bytes(fft_geom g, int64_t* bytes);
+fft_status fft_cg_save(fft_geom g, void* host_buf, int64_t bytes, void* stream);
+fft_status fft_cg_load(fft_geom g, const void* host_buf, int64_t bytes, void* stream);
+
+/*
  * fft_psf_batch - Hessian point-spread functions (Sec. II-D, Eq. resolution_2):
  *   out[(s * n_spike + k) * V + v] = sum_{p in S_s} J[p, v] J[p, spike_vox[k]]
  * i.e. H_S e_k with a unit (1 m/s) spike, for every row subset S_s and spike k.

@@ -7,7 +7,8 @@ library's kernels. The functions mirror the C entry points:
 * ``fft_table_build``  - sample the Phi function of a source spectrum (Eq. Kernel_freq)
 * ``fft_geom_create``  - rows, voxel grid and tables -> an operator handle (Eq. forward_compact)
 * ``fft_J_apply`` / ``fft_JT_apply`` - d = J m and g = J^T d, entries rebuilt on the fly
-* ``fft_cg_solve``     - damped least squares by CGLS (Eq. leastSquare_misfit)
+* ``fft_cg_solve``     - damped least squares by CGLS (Eq. leastSquare_misfit);
+  ``fft_cg_continue``, ``fft_cg_save`` / ``fft_cg_load`` resume a solve or checkpoint it
 * ``fft_psf_batch``    - Hessian point-spread functions J_S^T J_S e_k (Eq. resolution_2)
 
 ``Table`` and ``Geometry`` wrap the handles; ``JFunction`` / ``jacobian_apply`` put J behind
@@ -306,6 +307,32 @@ class Geometry:
     def cg_status(self, stream=None) -> None:
         """Wait for the last solve on `stream` and raise FFTError if it broke down."""
         check(_lib.load().fft_cg_status(self.handle, _stream_handle(stream)))
+
+    def cg_continue(self, n_iter: int, m=None, with_history: bool = False, stream=None, check_status: bool = True):
+        """n_iter more CGLS iterations from the handle's state (fft_cg_continue); returns the
+        model (written into `m` when given)."""
+        torch = _torch()
+        if m is None:
+            m = torch.empty(self.V, device="cuda", dtype=torch.float32)
+        hist = np.empty(n_iter + 1) if with_history else None
+        check(_lib.load().fft_cg_continue(self.handle, int(n_iter), _dev_ptr(m, self.V, "m"),
+                                          None if hist is None else hist.ctypes.data, _stream_handle(stream)))
+        if hist is None and check_status:
+            self.cg_status(stream)
+        return (m, hist) if with_history else m
+
+    def cg_save(self, stream=None) -> np.ndarray:
+        """The handle's CG state as a host byte array (fft_cg_save), e.g. to write to a file."""
+        n = ctypes.c_int64()
+        check(_lib.load().fft_cg_state_bytes(self.handle, ctypes.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        check(_lib.load().fft_cg_save(self.handle, buf.ctypes.data, n.value, _stream_handle(stream)))
+        return buf
+
+    def cg_load(self, state, stream=None) -> None:
+        """Replace the handle's CG state by one saved with cg_save (fft_cg_load)."""
+        buf = np.ascontiguousarray(state, dtype=np.uint8)
+        check(_lib.load().fft_cg_load(self.handle, buf.ctypes.data, buf.size, _stream_handle(stream)))
 
     def psf_batch(self, spikes: Sequence[int], subsets: Sequence[np.ndarray], mode: int = 0, out=None, stream=None):
         torch = _torch()

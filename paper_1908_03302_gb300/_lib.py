@@ -87,6 +87,10 @@ SIGNATURES = {
     "fft_frob2": (ctypes.c_int, [_VP, ctypes.POINTER(_D)]),
     "fft_cg_solve": (ctypes.c_int, [_VP, _VP, _D, _I32, _VP, _VP, _VP]),
     "fft_cg_status": (ctypes.c_int, [_VP, _VP]),
+    "fft_cg_continue": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP]),
+    "fft_cg_state_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
+    "fft_cg_save": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
+    "fft_cg_load": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
     "fft_psf_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP, _I32, _VP, _I32, _VP, _VP]),
     "fft_psf_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _I32, _VP, _VP]),
     "fft_tc_selftest": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_D)]),

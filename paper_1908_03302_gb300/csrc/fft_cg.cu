@@ -8,9 +8,15 @@
 // into a CUDA graph (per iteration count) on a private stream and replayed on the caller's
 // stream; it touches only the handle's own buffers, so the graph is independent of the
 // caller's pointers.
+//
+// The state between iterations is (m, p, r, gamma, lambda) plus the breakdown flag:
+// fft_cg_continue runs more iterations from it, and fft_cg_save / fft_cg_load copy it to and
+// from a host buffer (a checkpoint), so that a solve stopped after k iterations and resumed
+// for n more gives the same bits as k + n iterations in one call.
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <cstring>
 #include <vector>
 
 #include "fft_common.cuh"
@@ -107,6 +113,9 @@ __global__ void cg_beta_kernel(double* __restrict__ scal, const double* __restri
 
 __global__ void set_lambda_kernel(double* scal, double lam) { scal[S_LAMBDA] = lam; }
 
+// hist[0] = gamma = |J^T r - lambda m|^2 of the state a continued loop starts from.
+__global__ void cg_hist0_kernel(const double* __restrict__ scal, double* __restrict__ hist) { hist[0] = scal[S_GAMMA]; }
+
 // r = d - q
 __global__ void residual_kernel(const float* __restrict__ d, const float* __restrict__ q, int64_t M,
                                 float* __restrict__ r) {
@@ -179,10 +188,16 @@ fft_status ensure_workspace(fft_geom g, int32_t n_iter) {
         g->cg_hist = nullptr;
         if ((rc = cg_alloc(&g->cg_hist, (size_t)n_iter + 1)) != FFT_OK) return rc;
         g->cg_hist_cap = n_iter + 1;
+        // captured loops write the old history buffer: capture again
         if (g->cg_graph) {
             cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph);
             g->cg_graph = nullptr;
             g->cg_graph_iters = -1;
+        }
+        if (g->cg_graph_cont) {
+            cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph_cont);
+            g->cg_graph_cont = nullptr;
+            g->cg_graph_cont_iters = -1;
         }
     }
     if (!g->cg_stream) {
@@ -193,20 +208,11 @@ fft_status ensure_workspace(fft_geom g, int32_t n_iter) {
     return FFT_OK;
 }
 
-// Enqueue the whole solve on `st` using only handle buffers (cg_d, cg_m in; cg_m out).
-fft_status enqueue_solve(fft_geom g, int32_t n_iter, cudaStream_t st) {
+// The iteration loop from the handle's state (m, p, r, gamma, lambda); hist[it + 1] receives
+// |s|^2 after iteration it.
+fft_status enqueue_iterations(fft_geom g, int32_t n_iter, cudaStream_t st) {
     const int64_t M = g->M, V = g->V;
-    const unsigned rb = (unsigned)ceil_div(M, 256);
     fft_status rc;
-    FFT_CUDA(cudaMemsetAsync(g->cg_status, 0, sizeof(int32_t), st));
-    // r = d - J m
-    if ((rc = launch_J(g, g->cg_m, g->cg_q, st)) != FFT_OK) return rc;
-    residual_kernel<<<rb, 256, 0, st>>>(g->cg_d, g->cg_q, M, g->cg_r);
-    // s = J^T r - lambda m; gamma = |s|^2; p = s
-    if ((rc = launch_JT(g, g->cg_r, g->cg_s, st)) != FFT_OK) return rc;
-    cg_s_kernel<<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(g->cg_s, g->cg_m, V, g->cg_scal, g->cg_dots);
-    cg_beta_kernel<<<1, DOT_THREADS, 0, st>>>(g->cg_scal, g->cg_dots, g->cg_hist, 0, g->cg_status, 1);
-    FFT_CUDA(cudaMemcpyAsync(g->cg_p, g->cg_s, sizeof(float) * V, cudaMemcpyDeviceToDevice, st));
     for (int32_t it = 0; it < n_iter; ++it) {
         // q = J p; delta = |q|^2 + lambda |p|^2; alpha = gamma / delta
         if ((rc = launch_J(g, g->cg_p, g->cg_q, st)) != FFT_OK) return rc;
@@ -224,6 +230,70 @@ fft_status enqueue_solve(fft_geom g, int32_t n_iter, cudaStream_t st) {
     FFT_CUDA(cudaGetLastError());
     return FFT_OK;
 }
+
+// Enqueue the whole solve on `st` using only handle buffers (cg_d, cg_m in; cg_m out).
+fft_status enqueue_solve(fft_geom g, int32_t n_iter, cudaStream_t st) {
+    const int64_t M = g->M, V = g->V;
+    const unsigned rb = (unsigned)ceil_div(M, 256);
+    fft_status rc;
+    FFT_CUDA(cudaMemsetAsync(g->cg_status, 0, sizeof(int32_t), st));
+    // r = d - J m
+    if ((rc = launch_J(g, g->cg_m, g->cg_q, st)) != FFT_OK) return rc;
+    residual_kernel<<<rb, 256, 0, st>>>(g->cg_d, g->cg_q, M, g->cg_r);
+    // s = J^T r - lambda m; gamma = |s|^2; p = s
+    if ((rc = launch_JT(g, g->cg_r, g->cg_s, st)) != FFT_OK) return rc;
+    cg_s_kernel<<<DOT_BLOCKS, DOT_THREADS, 0, st>>>(g->cg_s, g->cg_m, V, g->cg_scal, g->cg_dots);
+    cg_beta_kernel<<<1, DOT_THREADS, 0, st>>>(g->cg_scal, g->cg_dots, g->cg_hist, 0, g->cg_status, 1);
+    FFT_CUDA(cudaMemcpyAsync(g->cg_p, g->cg_s, sizeof(float) * V, cudaMemcpyDeviceToDevice, st));
+    return enqueue_iterations(g, n_iter, st);
+}
+
+// Capture `enqueue` (n_iter iterations) into the graph held in *slot unless it already holds
+// that many, then launch it on `st`.
+template <typename F>
+fft_status run_graph(fft_geom g, void** slot, int32_t* slot_iters, int32_t n_iter, F enqueue, cudaStream_t st) {
+    if (!*slot || *slot_iters != n_iter) {
+        if (*slot) {
+            cudaGraphExecDestroy((cudaGraphExec_t)*slot);
+            *slot = nullptr;
+            *slot_iters = -1;
+        }
+        cudaStream_t cs = (cudaStream_t)g->cg_stream;
+        cudaGraph_t graph = nullptr;
+        FFT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        fft_status crc = enqueue(cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (crc != FFT_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return crc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        *slot = exec;
+        *slot_iters = n_iter;
+    }
+    FFT_CUDA(cudaGraphLaunch((cudaGraphExec_t)*slot, st));
+    return FFT_OK;
+}
+
+// Header of a saved CG state (fft_cg_save), followed by m (V floats), p (V) and r (M).
+struct CgStateHeader {
+    uint32_t magic;      // CG_STATE_MAGIC
+    uint32_t version;    // 1
+    int64_t n_rows, n_vox;
+    int64_t iterations;  // iterations behind the state
+    int32_t status;      // 0 or FFT_ERR_BREAKDOWN
+    int32_t reserved0;
+    double gamma, lambda;
+    double reserved1;
+};
+static_assert(sizeof(CgStateHeader) == 64, "CG state header: 64 bytes");
+constexpr uint32_t CG_STATE_MAGIC = 0x47434646u;   // "FFCG"
+
+int64_t cg_state_bytes(fft_geom g) { return (int64_t)sizeof(CgStateHeader) + (int64_t)sizeof(float) * (2 * g->V + g->M); }
 
 }  // namespace
 
@@ -244,34 +314,16 @@ extern "C" fft_status fft_cg_solve(fft_geom g, const float* d_dev, double lambda
     if ((rc = fft_frob2(g, &fro)) != FFT_OK) return rc;
     const double lam = lambda_rel * fro / (double)g->V;
 
+    g->cg_done = -1;   // the handle's state is overwritten from here on
     FFT_CUDA(cudaMemcpyAsync(g->cg_d, d_dev, sizeof(float) * g->M, cudaMemcpyDeviceToDevice, st));
     FFT_CUDA(cudaMemcpyAsync(g->cg_m, m_dev, sizeof(float) * g->V, cudaMemcpyDeviceToDevice, st));
     set_lambda_kernel<<<1, 1, 0, st>>>(g->cg_scal, lam);
     FFT_CUDA(cudaGetLastError());
 
-    if (!g->cg_graph || g->cg_graph_iters != n_iter) {
-        if (g->cg_graph) {
-            cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph);
-            g->cg_graph = nullptr;
-        }
-        cudaStream_t cs = (cudaStream_t)g->cg_stream;
-        cudaGraph_t graph = nullptr;
-        FFT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        fft_status crc = enqueue_solve(g, n_iter, cs);
-        cudaError_t e = cudaStreamEndCapture(cs, &graph);
-        if (crc != FFT_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return crc;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        g->cg_graph = exec;
-        g->cg_graph_iters = n_iter;
-    }
-    FFT_CUDA(cudaGraphLaunch((cudaGraphExec_t)g->cg_graph, st));
+    rc = run_graph(g, &g->cg_graph, &g->cg_graph_iters, n_iter,
+                   [&](cudaStream_t cs) { return enqueue_solve(g, n_iter, cs); }, st);
+    if (rc != FFT_OK) return rc;
+    g->cg_done = n_iter;
     FFT_CUDA(cudaMemcpyAsync(m_dev, g->cg_m, sizeof(float) * g->V, cudaMemcpyDeviceToDevice, st));
     if (!hist_host) return FFT_OK;   // asynchronous: fft_cg_status reports the outcome
     FFT_CUDA(cudaMemcpyAsync(hist_host, g->cg_hist, sizeof(double) * (n_iter + 1), cudaMemcpyDeviceToHost, st));
@@ -291,5 +343,99 @@ extern "C" fft_status fft_cg_status(fft_geom g, void* stream) {
         set_error("fft_cg_solve: breakdown (non-positive curvature or non-finite scalar)");
         return FFT_ERR_BREAKDOWN;
     }
+    return FFT_OK;
+}
+
+extern "C" fft_status fft_cg_continue(fft_geom g, int32_t n_iter, float* m_dev, double* hist_host, void* stream) {
+    FFT_ARG(g && m_dev, "fft_cg_continue: null argument");
+    FFT_ARG(n_iter >= 0 && n_iter <= 100000, "fft_cg_continue: n_iter must be in [0, 100000]");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    if (g->cg_done < 0) {
+        set_error("fft_cg_continue: the handle holds no CG state (run fft_cg_solve or fft_cg_load first)");
+        return FFT_ERR_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = ensure_workspace(g, n_iter)) != FFT_OK) return rc;
+    rc = run_graph(g, &g->cg_graph_cont, &g->cg_graph_cont_iters, n_iter,
+                   [&](cudaStream_t cs) {
+                       cg_hist0_kernel<<<1, 1, 0, cs>>>(g->cg_scal, g->cg_hist);
+                       return enqueue_iterations(g, n_iter, cs);
+                   },
+                   st);
+    if (rc != FFT_OK) return rc;
+    g->cg_done += n_iter;
+    FFT_CUDA(cudaMemcpyAsync(m_dev, g->cg_m, sizeof(float) * g->V, cudaMemcpyDeviceToDevice, st));
+    if (!hist_host) return FFT_OK;   // asynchronous: fft_cg_status reports the outcome
+    FFT_CUDA(cudaMemcpyAsync(hist_host, g->cg_hist, sizeof(double) * (n_iter + 1), cudaMemcpyDeviceToHost, st));
+    return fft_cg_status(g, stream);
+}
+
+extern "C" fft_status fft_cg_state_bytes(fft_geom g, int64_t* bytes) {
+    FFT_ARG(g && bytes, "fft_cg_state_bytes: null argument");
+    *bytes = cg_state_bytes(g);
+    return FFT_OK;
+}
+
+extern "C" fft_status fft_cg_save(fft_geom g, void* host_buf, int64_t bytes, void* stream) {
+    FFT_ARG(g && host_buf, "fft_cg_save: null argument");
+    FFT_ARG(bytes >= cg_state_bytes(g), "fft_cg_save: buffer smaller than fft_cg_state_bytes");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    if (g->cg_done < 0) {
+        set_error("fft_cg_save: the handle holds no CG state (run fft_cg_solve first)");
+        return FFT_ERR_STATE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double scal[8];
+    int32_t status = 0;
+    FFT_CUDA(cudaMemcpyAsync(scal, g->cg_scal, sizeof(scal), cudaMemcpyDeviceToHost, st));
+    FFT_CUDA(cudaMemcpyAsync(&status, g->cg_status, sizeof(status), cudaMemcpyDeviceToHost, st));
+    unsigned char* buf = static_cast<unsigned char*>(host_buf);
+    float* vec = reinterpret_cast<float*>(buf + sizeof(CgStateHeader));
+    FFT_CUDA(cudaMemcpyAsync(vec, g->cg_m, sizeof(float) * g->V, cudaMemcpyDeviceToHost, st));
+    FFT_CUDA(cudaMemcpyAsync(vec + g->V, g->cg_p, sizeof(float) * g->V, cudaMemcpyDeviceToHost, st));
+    FFT_CUDA(cudaMemcpyAsync(vec + 2 * g->V, g->cg_r, sizeof(float) * g->M, cudaMemcpyDeviceToHost, st));
+    FFT_CUDA(cudaStreamSynchronize(st));
+    CgStateHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = CG_STATE_MAGIC;
+    h.version = 1;
+    h.n_rows = g->M;
+    h.n_vox = g->V;
+    h.iterations = g->cg_done;
+    h.status = status;
+    h.gamma = scal[S_GAMMA];
+    h.lambda = scal[S_LAMBDA];
+    memcpy(buf, &h, sizeof(h));
+    return FFT_OK;
+}
+
+extern "C" fft_status fft_cg_load(fft_geom g, const void* host_buf, int64_t bytes, void* stream) {
+    FFT_ARG(g && host_buf, "fft_cg_load: null argument");
+    FFT_ARG(bytes >= (int64_t)sizeof(CgStateHeader), "fft_cg_load: buffer shorter than a CG state header");
+    CgStateHeader h;
+    memcpy(&h, host_buf, sizeof(h));
+    FFT_ARG(h.magic == CG_STATE_MAGIC && h.version == 1, "fft_cg_load: not a CG state saved by fft_cg_save");
+    FFT_ARG(h.n_rows == g->M && h.n_vox == g->V, "fft_cg_load: the state is for another geometry size");
+    FFT_ARG(bytes >= cg_state_bytes(g), "fft_cg_load: buffer shorter than the state");
+    FFT_ARG(h.iterations >= 0 && (h.status == 0 || h.status == FFT_ERR_BREAKDOWN) && h.lambda >= 0.0,
+            "fft_cg_load: corrupt CG state header");
+    fft_status rc = check_device(g->dev);
+    if (rc != FFT_OK) return rc;
+    if ((rc = ensure_workspace(g, 0)) != FFT_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    double scal[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    scal[S_GAMMA] = h.gamma;
+    scal[S_LAMBDA] = h.lambda;
+    const int32_t status = h.status;
+    const float* vec = reinterpret_cast<const float*>(static_cast<const unsigned char*>(host_buf) + sizeof(CgStateHeader));
+    FFT_CUDA(cudaMemcpyAsync(g->cg_scal, scal, sizeof(scal), cudaMemcpyHostToDevice, st));
+    FFT_CUDA(cudaMemcpyAsync(g->cg_status, &status, sizeof(status), cudaMemcpyHostToDevice, st));
+    FFT_CUDA(cudaMemcpyAsync(g->cg_m, vec, sizeof(float) * g->V, cudaMemcpyHostToDevice, st));
+    FFT_CUDA(cudaMemcpyAsync(g->cg_p, vec + g->V, sizeof(float) * g->V, cudaMemcpyHostToDevice, st));
+    FFT_CUDA(cudaMemcpyAsync(g->cg_r, vec + 2 * g->V, sizeof(float) * g->M, cudaMemcpyHostToDevice, st));
+    FFT_CUDA(cudaStreamSynchronize(st));
+    g->cg_done = h.iterations;
     return FFT_OK;
 }

@@ -168,6 +168,9 @@ struct fft_geom_s {
     int32_t cg_hist_cap = 0;
     void* cg_graph = nullptr;            // cudaGraphExec_t of the iteration loop
     int32_t cg_graph_iters = -1;
+    void* cg_graph_cont = nullptr;       // cudaGraphExec_t of a continued loop (fft_cg_continue)
+    int32_t cg_graph_cont_iters = -1;
+    int64_t cg_done = -1;                // iterations behind the handle's CG state (-1: no state)
     void* cg_stream = nullptr;           // private capture stream
 };
 

@@ -235,6 +235,7 @@ void free_geom(fft_geom g) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->cg_graph) cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph);
+    if (g->cg_graph_cont) cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph_cont);
     if (g->cg_stream) cudaStreamDestroy((cudaStream_t)g->cg_stream);
     delete g;
 }
@@ -317,6 +318,11 @@ fft_status build_items(fft_geom g, const std::vector<int64_t>& toff, int items_p
         cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph);
         g->cg_graph = nullptr;
         g->cg_graph_iters = -1;
+    }
+    if (g->cg_graph_cont) {
+        cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph_cont);
+        g->cg_graph_cont = nullptr;
+        g->cg_graph_cont_iters = -1;
     }
     return FFT_OK;
 }
