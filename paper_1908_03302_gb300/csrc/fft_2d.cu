@@ -49,6 +49,7 @@ fft_status vol_scratch(fft_geom g, float** out) {
 using namespace fftgb;
 
 extern "C" fft_status fft_J2d_apply(fft_geom g, const float* m2_dev, float* d_dev, void* stream) {
+    FFT_API_RANGE("fft_J2d_apply");
     FFT_ARG(g && m2_dev && d_dev, "fft_J2d_apply: null argument");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
@@ -62,6 +63,7 @@ extern "C" fft_status fft_J2d_apply(fft_geom g, const float* m2_dev, float* d_de
 }
 
 extern "C" fft_status fft_JT2d_apply(fft_geom g, const float* d_dev, float* g2_dev, void* stream) {
+    FFT_API_RANGE("fft_JT2d_apply");
     FFT_ARG(g && d_dev && g2_dev, "fft_JT2d_apply: null argument");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;

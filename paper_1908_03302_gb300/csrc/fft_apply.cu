@@ -1229,6 +1229,7 @@ fft_status compute_frob2(fft_geom g, double* out) {
 using namespace fftgb;
 
 extern "C" fft_status fft_J_apply(fft_geom g, const float* m_dev, float* d_dev, void* stream) {
+    FFT_API_RANGE("fft_J_apply");
     FFT_ARG(g && m_dev && d_dev, "fft_J_apply: null argument");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
@@ -1236,6 +1237,7 @@ extern "C" fft_status fft_J_apply(fft_geom g, const float* m_dev, float* d_dev, 
 }
 
 extern "C" fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev, void* stream) {
+    FFT_API_RANGE("fft_JT_apply");
     FFT_ARG(g && d_dev && g_dev, "fft_JT_apply: null argument");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
@@ -1243,6 +1245,7 @@ extern "C" fft_status fft_JT_apply(fft_geom g, const float* d_dev, float* g_dev,
 }
 
 extern "C" fft_status fft_J_apply_batch(fft_geom g, const float* m_dev, int32_t n, float* d_dev, void* stream) {
+    FFT_API_RANGE("fft_J_apply_batch");
     FFT_ARG(g && m_dev && d_dev, "fft_J_apply_batch: null argument");
     FFT_ARG(n >= 1, "fft_J_apply_batch: need n >= 1 columns");
     fft_status rc = check_device(g->dev);
@@ -1251,6 +1254,7 @@ extern "C" fft_status fft_J_apply_batch(fft_geom g, const float* m_dev, int32_t 
 }
 
 extern "C" fft_status fft_JT_apply_batch(fft_geom g, const float* d_dev, int32_t n, float* g_dev, void* stream) {
+    FFT_API_RANGE("fft_JT_apply_batch");
     FFT_ARG(g && d_dev && g_dev, "fft_JT_apply_batch: null argument");
     FFT_ARG(n >= 1, "fft_JT_apply_batch: need n >= 1 columns");
     fft_status rc = check_device(g->dev);
@@ -1259,6 +1263,7 @@ extern "C" fft_status fft_JT_apply_batch(fft_geom g, const float* d_dev, int32_t
 }
 
 extern "C" fft_status fft_coverage(fft_geom g, const float* w_dev, float* cov_dev, void* stream) {
+    FFT_API_RANGE("fft_coverage");
     FFT_ARG(g && cov_dev, "fft_coverage: null argument");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
@@ -1266,6 +1271,7 @@ extern "C" fft_status fft_coverage(fft_geom g, const float* w_dev, float* cov_de
 }
 
 extern "C" fft_status fft_frob2(fft_geom g, double* out) {
+    FFT_API_RANGE("fft_frob2");
     FFT_ARG(g && out, "fft_frob2: null argument");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;

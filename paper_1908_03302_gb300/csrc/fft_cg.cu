@@ -303,6 +303,7 @@ using namespace fftgb;
 
 extern "C" fft_status fft_cg_solve(fft_geom g, const float* d_dev, double lambda_rel, int32_t n_iter,
                                    float* m_dev, double* hist_host, void* stream) {
+    FFT_API_RANGE("fft_cg_solve");
     FFT_ARG(g && d_dev && m_dev, "fft_cg_solve: null argument");
     FFT_ARG(n_iter >= 0 && n_iter <= 100000, "fft_cg_solve: n_iter must be in [0, 100000]");
     FFT_ARG(lambda_rel >= 0 && isfinite(lambda_rel), "fft_cg_solve: lambda_rel must be >= 0");
@@ -347,6 +348,7 @@ extern "C" fft_status fft_cg_status(fft_geom g, void* stream) {
 }
 
 extern "C" fft_status fft_cg_continue(fft_geom g, int32_t n_iter, float* m_dev, double* hist_host, void* stream) {
+    FFT_API_RANGE("fft_cg_continue");
     FFT_ARG(g && m_dev, "fft_cg_continue: null argument");
     FFT_ARG(n_iter >= 0 && n_iter <= 100000, "fft_cg_continue: n_iter must be in [0, 100000]");
     fft_status rc = check_device(g->dev);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -28,6 +29,18 @@ fft_status cuda_fail(cudaError_t e, const char* what);
             return FFT_ERR_ARG;             \
         }                                   \
     } while (0)
+
+// ------------------------------------------------------------------ tracing
+// An NVTX range named after the C-ABI call around its body, so that profiler timelines and
+// `ncu --nvtx --nvtx-include "<name>/"` can pick out the kernels of one call. Without a
+// profiler attached the push and pop cost a function call each.
+struct ApiRange {
+    explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange&) = delete;
+    ApiRange& operator=(const ApiRange&) = delete;
+};
+#define FFT_API_RANGE(name) ::fftgb::ApiRange fft_api_range_(name)
 
 // ------------------------------------------------------------------ tiling constants
 // A tile is 16 x 16 x 8 voxels handled by one CTA of 8 warps. Warp w owns the 8 x 8 x 4

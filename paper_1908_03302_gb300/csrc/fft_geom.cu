@@ -335,6 +335,7 @@ extern "C" fft_status fft_geom_create(const double* tx_xyz, int32_t n_tx, const 
                                       int64_t n_rows, const int32_t* band_of_row, const fft_grid* grid,
                                       double c0, const fft_table* tables, int32_t n_tables,
                                       int32_t dt_mode, fft_geom* out) {
+    FFT_API_RANGE("fft_geom_create");
     FFT_ARG(out, "fft_geom_create: null out");
     *out = nullptr;
     FFT_ARG(tx_xyz && n_tx >= 2, "fft_geom_create: need at least two transducers");

@@ -250,6 +250,7 @@ using namespace fftgb;
 extern "C" fft_status fft_hessian_lowrank(fft_geom g, const float* omega_dev, int32_t ell, int32_t k,
                                           int32_t n_power, double sigma, float* vecs_dev, double* eigvals,
                                           void* stream) {
+    FFT_API_RANGE("fft_hessian_lowrank");
     FFT_ARG(g && omega_dev && vecs_dev && eigvals, "fft_hessian_lowrank: null argument");
     FFT_ARG(ell >= 1 && ell <= MAX_ELL && k >= 1 && k <= ell, "fft_hessian_lowrank: need 1 <= k <= ell <= 256");
     FFT_ARG(n_power >= 0 && n_power <= 64, "fft_hessian_lowrank: n_power must be in [0, 64]");
@@ -312,6 +313,7 @@ extern "C" fft_status fft_hessian_lowrank(fft_geom g, const float* omega_dev, in
 
 extern "C" fft_status fft_lowrank_diag(fft_geom g, const float* vecs_dev, const double* eigvals, int32_t k,
                                        double alpha, float* post_dev, float* res_dev, void* stream) {
+    FFT_API_RANGE("fft_lowrank_diag");
     FFT_ARG(g && vecs_dev && eigvals, "fft_lowrank_diag: null argument");
     FFT_ARG(k >= 1 && k <= MAX_ELL, "fft_lowrank_diag: need 1 <= k <= 256");
     FFT_ARG(alpha > 0 && isfinite(alpha), "fft_lowrank_diag: alpha must be > 0");

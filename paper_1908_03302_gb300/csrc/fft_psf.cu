@@ -284,6 +284,7 @@ fft_status psf_fp32_batched(fft_geom g, const int64_t* spike_vox, int32_t n_spik
 extern "C" fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
                                     const int32_t* subset_off, int32_t n_subsets, const int32_t* subset_rows,
                                     int32_t mode, float* out_dev, void* stream) {
+    FFT_API_RANGE("fft_psf_batch");
     FFT_ARG(g && spike_vox && subset_off && out_dev, "fft_psf_batch: null argument");
     FFT_ARG(n_spike >= 1 && n_subsets >= 1, "fft_psf_batch: need at least one spike and one subset");
     FFT_ARG(mode >= 0 && mode <= 2,

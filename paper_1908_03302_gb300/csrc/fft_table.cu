@@ -81,6 +81,7 @@ using namespace fftgb;
 
 extern "C" fft_status fft_table_build(const fft_spectrum* spec, int32_t n_samples, double dt_max,
                                       double* host_out, fft_table* out) {
+    FFT_API_RANGE("fft_table_build");
     FFT_ARG(spec && out, "fft_table_build: null spec or out");
     FFT_ARG(n_samples >= 2 && n_samples <= 65536, "fft_table_build: n_samples must be in [2, 65536]");
     FFT_ARG(dt_max > 0 && isfinite(dt_max), "fft_table_build: dt_max must be > 0");
@@ -176,6 +177,7 @@ extern "C" void fft_table_destroy(fft_table t) {
 // even Gaussian W the denominator is int_0^inf w^2 W dw = sqrt(2 pi) s (w0^2 + s^2).
 extern "C" fft_status fft_trig_build(const fft_spectrum* spec, double dt_max, int32_t n_terms, double* coef_out,
                                      double* dw_out, int32_t* n_terms_out, fft_table* out) {
+    FFT_API_RANGE("fft_trig_build");
     FFT_ARG(spec && out, "fft_trig_build: null spec or out");
     FFT_ARG(dt_max > 0 && isfinite(dt_max), "fft_trig_build: dt_max must be > 0");
     FFT_ARG(spec->kind == 0, "fft_trig_build: the sine series needs a Gaussian spectrum (kind 0)");

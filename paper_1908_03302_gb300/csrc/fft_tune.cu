@@ -27,6 +27,7 @@ __global__ void tune_fill_kernel(float* x, int64_t n, float scale) {
 using namespace fftgb;
 
 extern "C" fft_status fft_geom_autotune(fft_geom g, void* stream, fft_tune_info_t* info) {
+    FFT_API_RANGE("fft_geom_autotune");
     FFT_ARG(g, "fft_geom_autotune: null geometry");
     fft_status rc = check_device(g->dev);
     if (rc != FFT_OK) return rc;
