@@ -141,6 +141,40 @@ def slice_rings(n_tx: int, radius: float, z_positions: Sequence[float]) -> Tuple
     return tx, pairs
 
 
+def roi_pixels(radius: float, h: float, half_offset: bool = False) -> np.ndarray:
+    """In-plane pixel centres of a 2-D inversion grid over a circular region of interest
+    (Sec. IV's lab inversion: 1 mm pixels over a 70 mm-radius ROI): the points (i h, j h) with
+    x^2 + y^2 <= radius^2, or ((i + 1/2) h, (j + 1/2) h) with ``half_offset``. Returned as an
+    (n, 2) array, x fastest. The test is exact in integers when radius / h is an integer."""
+    q = radius / h
+    n = int(math.floor(q)) + 1
+    k = np.arange(-n, n + 1, dtype=np.int64)
+    if half_offset:
+        a = 2 * k + 1                     # 2 (k + 1/2): twice the coordinate in pixels
+        ax, ay = np.meshgrid(a, a)
+        if abs(q - round(q)) < 1e-9:
+            inside = ax * ax + ay * ay <= 4 * round(q) ** 2
+        else:
+            inside = (ax * ax + ay * ay) <= (2.0 * q) ** 2
+        xy = np.stack([ax[inside], ay[inside]], axis=1) * (0.5 * h)
+    else:
+        ix, iy = np.meshgrid(k, k)
+        if abs(q - round(q)) < 1e-9:
+            inside = ix * ix + iy * iy <= round(q) ** 2
+        else:
+            inside = (ix * ix + iy * iy) <= q * q
+        xy = np.stack([ix[inside], iy[inside]], axis=1) * h
+    return xy.astype(np.float64)
+
+
+def lab_ascan_count(n_emitters: int = 16, n_receivers: int = 16, n_positions: int = 11,
+                    n_rotations: int = 23) -> int:
+    """A-scans of Sec. IV's lab acquisition: two 16-element arrays (every emitter of one to
+    every receiver of the other), 11 receiver-array positions and 23 rotations of the
+    set-up. One traveltime, i.e. one row of the forward operator, per A-scan."""
+    return n_emitters * n_receivers * n_positions * n_rotations
+
+
 # --------------------------------------------------------------------------- phantoms
 
 def blobs_model(grid: Grid, seed: int, n_blobs: int = 5, amp: float = 30.0,
