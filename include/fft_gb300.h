@@ -363,9 +363,11 @@ fft_status fft_cg_load(fft_geom g, const void* host_buf, int64_t bytes, void* st
  *                    each 8 x 4 x 4 voxel brick in FP32, rounds it and D to BF16 and issues
  *                    tcgen05.mma (96 rows of one group per chunk, N = the spikes of a launch)
  *                    accumulating each group in FP32 in its own tensor-memory columns; each
- *                    PSF is the sum of its subset's groups. Up to 144 spikes per launch with 3
- *                    groups (more run in blocks of spikes); with more than 32 groups the
- *                    subsets are taken one at a time. Relative L2 error ~1e-3 (BF16 operands);
+ *                    PSF is the sum of its subset's groups. A launch takes as many spikes as fit
+ *                    groups x spikes (rounded up to 16) <= 512 accumulator columns and the
+ *                    shared memory (144 with 3 groups and three band tables); more run in
+ *                    blocks of spikes. With more than 32 groups the subsets are taken one at
+ *                    a time. Relative L2 error ~1e-3 (BF16 operands);
  *                    the cut of a band whose Phi does not vanish at dt_max is taken in FP32
  *                    here (the FP32 paths re-decide it in FP64). At most 32 subsets; a subset
  *                    must not list a row twice (FFT_ERR_ARG). FFT_ERR_TIMEOUT if a bounded wait
