@@ -89,6 +89,7 @@ struct PsfTcParams {
     int n_bands, n_tab;
     const int32_t* tile_rows;
     const int64_t* tile_off;
+    const int32_t* tile_order;  // the pre-passes' CTA -> tile, heaviest tiles first
     const float4* ebase;
     const float* ebase3;
     const uint8_t* grp;        // group of each row (0xFF: the row is in no subset)
@@ -212,7 +213,7 @@ constexpr int MASK_THREADS = 256;
 // entries, by the row's group (an upper bound of the compact candidates psf_mask_kernel keeps).
 __global__ void __launch_bounds__(MASK_THREADS) psf_cap_kernel(const PsfTcParams P, int32_t* __restrict__ cap) {
     __shared__ int s_cnt[PSF_TC_MAX_GROUPS];
-    const int T = blockIdx.x, G = P.n_groups;
+    const int T = P.tile_order[blockIdx.x], G = P.n_groups;
     if (threadIdx.x < PSF_TC_MAX_GROUPS) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     for (int64_t e = P.tile_off[T] + threadIdx.x; e < P.tile_off[T + 1]; e += MASK_THREADS) {
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(MASK_THREADS) psf_mask_kernel(const PsfTcParam
     __shared__ int wsum[PSF_TC_MAX_GROUPS][MASK_THREADS / 32];
     __shared__ int64_t run[PSF_TC_MAX_GROUPS];
     __shared__ unsigned int s_or;
-    const int T = blockIdx.x, G = P.n_groups;
+    const int T = P.tile_order[blockIdx.x], G = P.n_groups;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tx = T % P.tiles_x, ty = (T / P.tiles_x) % P.tiles_y, tz = T / (P.tiles_x * P.tiles_y);
     const int64_t e_begin = P.tile_off[T], e_end = P.tile_off[T + 1];
@@ -911,7 +912,7 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent
     // lists, then the units: the sub-bricks that some candidate of their tile may reach,
     // heaviest tiles first
     const int64_t n_seg = g->n_tiles * n_groups;
-    int32_t *c_cnt = nullptr, *d_units = nullptr, *d_ctr = nullptr, *d_cap = nullptr;
+    int32_t *c_cnt = nullptr, *d_units = nullptr, *d_ctr = nullptr, *d_cap = nullptr, *d_order = nullptr;
     int64_t* d_seg = nullptr;
     float4* c_rec = nullptr;
     uint16_t* c_or = nullptr;
@@ -925,8 +926,21 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent
         cudaFree(d_ctr);
         cudaFree(d_cap);
         cudaFree(d_seg);
+        cudaFree(d_order);
     };
-    cudaError_t e = cudaMalloc(&d_cap, sizeof(int32_t) * (size_t)n_seg);
+    // the pre-passes run one CTA per tile; tiles differ in size by orders of magnitude, so
+    // the heaviest start first and the small ones fill in behind them
+    std::vector<int64_t> toff(g->n_tiles + 1);
+    std::vector<int32_t> order(g->n_tiles);
+    cudaError_t e = cudaMemcpy(toff.data(), g->tile_off, sizeof(int64_t) * toff.size(), cudaMemcpyDeviceToHost);
+    for (int64_t T = 0; T < g->n_tiles; ++T) order[T] = (int32_t)T;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return toff[a + 1] - toff[a] > toff[b + 1] - toff[b]; });
+    if (e == cudaSuccess) e = cudaMalloc(&d_order, sizeof(int32_t) * (size_t)g->n_tiles);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, st);
+    P.tile_order = d_order;
+    if (e == cudaSuccess) e = cudaMalloc(&d_cap, sizeof(int32_t) * (size_t)n_seg);
     if (e == cudaSuccess) e = cudaMalloc(&d_seg, sizeof(int64_t) * (size_t)n_seg);
     if (e == cudaSuccess) e = cudaMalloc(&c_cnt, sizeof(int32_t) * (size_t)n_seg);
     if (e == cudaSuccess) e = cudaMalloc(&c_or, sizeof(uint16_t) * (size_t)g->n_tiles);
