@@ -379,7 +379,10 @@ fft_status fft_cg_load(fft_geom g, const void* host_buf, int64_t bytes, void* st
  *   out_dev       device float32[n_subsets * n_spike * V], written entirely.
  * Allocates its scratch (row lists, the columns of D, staging) with cudaMalloc on every call
  * and synchronises with `stream` before returning; see fft_psf_noalloc for a variant that does
- * neither allocation.
+ * neither allocation. Mode 1 keeps one buffer in the handle instead, its candidate records
+ * (48 bytes per candidate row of a tile; 16 GB for 384 PSFs over 1.57 M rows and 6.29 M
+ * voxels): it grows to the largest call's need, counts in fft_geom_info's scratch_bytes and
+ * is freed by fft_geom_destroy.
  */
 fft_status fft_psf_batch(fft_geom g, const int64_t* spike_vox, int32_t n_spike,
                          const int32_t* subset_off, int32_t n_subsets,

@@ -175,6 +175,8 @@ struct fft_geom_s {
     double* cg_dots = nullptr;           // [2 * DOT_BLOCKS] partial inner products
     int32_t* cg_status = nullptr;        // [1]
     float* vol = nullptr;                // [V] volume scratch of the 2-D apply (allocated on first use)
+    float4* psf_crec = nullptr;          // candidate records of the tensor-core PSF path (grow-only)
+    int64_t psf_crec_cap = 0;            // its capacity in candidates (3 float4 each)
     float* jpart4 = nullptr;             // [E * 8 * 4] J partials of the four-column apply (first use)
     float* gpart4 = nullptr;             // [n_slots * 4 * TILE_VOX] J^T partials of the four-column apply
     double* cg_hist = nullptr;           // [cg_hist_cap]

@@ -231,7 +231,8 @@ void free_geom(fft_geom g) {
     void* ptrs[] = {g->d_band, g->rec, g->rec64, g->row_band, g->tab, g->tile_off, g->tile_rows, g->ebase, g->ebase3,
                     g->row_off, g->row_ent, g->items, g->tile_slot0, g->tile_nslot, g->jpart,
                     g->gpart, g->counter, g->cg_r, g->cg_q, g->cg_s, g->cg_p, g->cg_d, g->cg_m,
-                    g->cg_scal, g->cg_dots, g->cg_status, g->cg_hist, g->vol, g->jpart4, g->gpart4};
+                    g->cg_scal, g->cg_dots, g->cg_status, g->cg_hist, g->vol, g->jpart4, g->gpart4,
+                    g->psf_crec};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (g->cg_graph) cudaGraphExecDestroy((cudaGraphExec_t)g->cg_graph);

@@ -917,9 +917,8 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent
     float4* c_rec = nullptr;
     uint16_t* c_or = nullptr;
     float2* tab_tc = nullptr;
-    auto release = [&]() {
+    auto release = [&]() {   // (the candidate records stay with the geometry)
         cudaFree(tab_tc);
-        cudaFree(c_rec);
         cudaFree(c_cnt);
         cudaFree(c_or);
         cudaFree(d_units);
@@ -971,7 +970,20 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent
         release();
         return FFT_OK;
     }
-    if (e == cudaSuccess) e = cudaMalloc(&c_rec, 3 * sizeof(float4) * (size_t)n_cand);
+    // the candidate records (16 GB for psf3d) stay with the geometry and grow as needed:
+    // allocating and freeing them took ~9 ms per call
+    if (e == cudaSuccess && g->psf_crec_cap < n_cand) {
+        cudaFree(g->psf_crec);
+        g->scratch_bytes -= (int64_t)(3 * sizeof(float4)) * g->psf_crec_cap;
+        g->psf_crec = nullptr;
+        g->psf_crec_cap = 0;
+        e = cudaMalloc(&g->psf_crec, 3 * sizeof(float4) * (size_t)n_cand);
+        if (e == cudaSuccess) {
+            g->psf_crec_cap = n_cand;
+            g->scratch_bytes += (int64_t)(3 * sizeof(float4)) * n_cand;
+        }
+    }
+    c_rec = g->psf_crec;
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_seg, seg.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
         release();
