@@ -259,10 +259,22 @@ def run_psf(args, ws, rank, local):
     tensor = {"mma_tflops": mma_flops / tc_s / 1e12, "peak_tflops": peak_tc,
               "peak_basis": f"bf16 sustained ({pk_kind})", "frac": mma_flops / tc_s / 1e12 / peak_tc,
               "mma_flops_per_batch": mma_flops}
+    # what bounds the batch is generating the J tiles in FP32: generated entries per second of
+    # the whole call against the canonical FP32 issue rate of one evaluation (the J / J^T peak)
+    entries = float(geo.info().psf_tc_entries)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max = float(pk.get("sm_max_mhz") or 2070.0)
+    peak_evals = sm_count * FP32_LANES_PER_SM_CLK * sm_max * 1e6 / OPS_PER_EVAL
+    generation = {"bound": "alu", "achieved": entries / tc_s / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
+                  "frac": entries / tc_s / peak_evals, "traffic": None,
+                  "kernel": "psf_tc_kernel (J tiles generated in FP32, BF16 MMA), whole fft_psf_batch call",
+                  "entries_per_batch": entries,
+                  "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM_CLK} FP32 lanes x {sm_max:.0f} MHz "
+                                f"({pk_kind}) / {OPS_PER_EVAL} ops per eval"}
     if args.psf_tc_only:
         if rank == 0:
-            print(json.dumps({"psf_tc_ms": tc_ms, "geometry": w.name, "spikes": len(spikes), "tensor": tensor}),
-                  flush=True)
+            print(json.dumps({"psf_tc_ms": tc_ms, "geometry": w.name, "spikes": len(spikes), "tensor": tensor,
+                              "roofline": generation}), flush=True)
         return 0
     # FP32 path on a slice of the spikes (same per-PSF cost), scaled to the whole batch
     k32 = min(len(spikes), args.psf_fp32_spikes)
@@ -331,6 +343,7 @@ def run_psf(args, ws, rank, local):
         "fp32_batched_path": "four columns per J^T (fft_psf_batch mode 2), same spikes, scaled",
         "speedup_tc_vs_fp32_batched": fp4_full_ms / tc_avg,
         "tensor": tensor,
+        "roofline": generation,
         "tc_vs_fp32_rel_l2_max": max(diff) if diff else None,
         "err_vs_fp64_oracle": {"tc_rel_l2_max": max(errs_tc), "fp32_rel_l2_max": max(errs_fp),
                                "fp32_batched_rel_l2_max": max(errs_fp4),

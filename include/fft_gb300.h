@@ -157,6 +157,8 @@ typedef struct {
     int32_t phi_terms;       /* 0: sampled tables; else the largest sine-series length */
     double psf_tc_mma_flops; /* tensor-core MMA flops of the last fft_psf_batch call in mode 1:
                                 2 x 128 x 96 x N per chunk of generated J tile, N the MMA width */
+    double psf_tc_entries;   /* J entries that call generated: 128 voxels x 96 rows per chunk,
+                                the stand-in rows of partial chunks included */
 } fft_geom_info_t;
 fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info);
 

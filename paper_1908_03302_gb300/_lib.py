@@ -61,7 +61,7 @@ class fft_geom_info_t(ctypes.Structure):
                 ("n_items", ctypes.c_int64), ("support_evals", ctypes.c_int64),
                 ("scratch_bytes", ctypes.c_int64), ("dt_mode", ctypes.c_int32),
                 ("evaluated_evals", ctypes.c_int64), ("phi_terms", ctypes.c_int32),
-                ("psf_tc_mma_flops", ctypes.c_double)]
+                ("psf_tc_mma_flops", ctypes.c_double), ("psf_tc_entries", ctypes.c_double)]
 
 
 # (name, restype, argtypes) for every function declared in include/fft_gb300.h

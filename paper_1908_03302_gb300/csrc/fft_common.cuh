@@ -123,6 +123,7 @@ struct fft_geom_s {
     int32_t trig_nq = 0;                 // series: coefficient groups of 4 per band (padded)
     int32_t trig_terms = 0;              // series: the largest term count over the bands
     double psf_tc_mma_flops = 0.0;       // MMA flops of the last tensor-core fft_psf_batch call
+    double psf_tc_entries = 0.0;         // J entries it generated
     bool guard;                          // a (virtual) voxel centre coincides with a transducer
     bool sharp = false;                  // some band's Phi does not vanish at its cut-off
     fftgb::BandConst band[fftgb::MAX_BANDS];

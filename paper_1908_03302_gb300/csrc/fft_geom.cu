@@ -696,5 +696,6 @@ extern "C" fft_status fft_geom_info(fft_geom g, fft_geom_info_t* info) {
     info->dt_mode = g->dt_mode;
     info->phi_terms = g->trig_terms;
     info->psf_tc_mma_flops = g->psf_tc_mma_flops;
+    info->psf_tc_entries = g->psf_tc_entries;
     return FFT_OK;
 }

@@ -201,6 +201,7 @@ fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, co
             member[subset_rows[i]] |= 1u << s;
         }
     g->psf_tc_mma_flops = 0.0;
+    g->psf_tc_entries = 0.0;
     cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(float) * (size_t)n_subsets * n_spike * g->V, st);
     if (e != cudaSuccess) return cuda_fail(e, "fft_psf_batch (tensor cores)");
     std::vector<uint32_t> gmask;   // distinct non-empty sets, in order of first appearance

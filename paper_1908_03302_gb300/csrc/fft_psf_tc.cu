@@ -1062,6 +1062,7 @@ fft_status launch_psf_tc(fft_geom g, const int64_t* d_off, const uint32_t* d_ent
     memcpy(&nch, hs + 2, sizeof(nch));
     // MMA work of this launch: every chunk multiplies a 128 x KC BF16 tile by KC x ng
     g->psf_tc_mma_flops += 2.0 * 128.0 * KC * (double)ng * (double)nch;
+    g->psf_tc_entries += 128.0 * KC * (double)nch;
     release();
     if (e != cudaSuccess) return cuda_fail(e, "psf tensor-core path");
     if (status != 0) {
