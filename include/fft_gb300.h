@@ -329,6 +329,24 @@ fft_status fft_cg_status(fft_geom g, void* stream);
 fft_status fft_cg_continue(fft_geom g, int32_t n_iter, float* m_dev, double* hist_host, void* stream);
 
 /*
+ * fft_psf_row_groups - host only (no device work, no handle): the grouping of rows the
+ * tensor-core path of fft_psf_batch uses (Sec. II-D, Eq. resolution_2 summed group by group):
+ * rows are grouped by the set of subsets that hold them, so that the PSF of subset s is the
+ * sum of the groups whose set contains s.
+ *   n_rows        rows of the geometry (M).
+ *   subset_off, n_subsets, subset_rows   as in fft_psf_batch (1 .. 32 subsets).
+ *   grp           host uint8[n_rows] out: group of each row, 0xFF for a row in no subset.
+ *   gmask         host uint32[32] out: bit s of gmask[g] set if group g's rows are in subset s;
+ *                 groups numbered in order of their first row.
+ *   n_groups      out: the number of groups (<= 32), or -1 if there are more than 32 (grp and
+ *                 gmask then hold no complete grouping; fft_psf_batch then takes the subsets
+ *                 one at a time).
+ * FFT_ERR_ARG for a row outside [0, n_rows) or listed twice in one subset.
+ */
+fft_status fft_psf_row_groups(int64_t n_rows, const int32_t* subset_off, int32_t n_subsets,
+                              const int32_t* subset_rows, uint8_t* grp, uint32_t* gmask, int32_t* n_groups);
+
+/*
  * Checkpoint and resume of a solve (plumbing around the CGLS of Sec. II-D; the paper has no
  * counterpart). The state is (m, p, r, gamma, lambda, breakdown flag,
  * iterations done), stored in FP32 / FP64 exactly as the loop keeps it, so a state saved,

@@ -398,6 +398,25 @@ def fft_psf_batch(geom: Geometry, spikes, subsets, mode=0, out=None, stream=None
     return geom.psf_batch(spikes, subsets, mode, out, stream)
 
 
+def psf_row_groups(n_rows: int, subsets: Sequence[np.ndarray]):
+    """Rows grouped by the set of subsets that hold them (fft_psf_row_groups, host only):
+    returns (grp, gmask) with grp[p] the group of row p (255: in no subset) and gmask[g] the
+    subsets of group g as a bit mask, or (None, None) for more than 32 groups."""
+    off = np.zeros(len(subsets) + 1, dtype=np.int32)
+    off[1:] = np.cumsum([len(s) for s in subsets])
+    idx = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.int32) for s in subsets])
+                               if len(subsets) else np.zeros(0, np.int32), dtype=np.int32)
+    grp = np.empty(int(n_rows), dtype=np.uint8)
+    gmask = np.zeros(32, dtype=np.uint32)
+    ng = ctypes.c_int32()
+    check(_lib.load().fft_psf_row_groups(int(n_rows), off.ctypes.data, len(subsets),
+                                         idx.ctypes.data if len(idx) else None, grp.ctypes.data,
+                                         gmask.ctypes.data, ctypes.byref(ng)))
+    if ng.value < 0:
+        return None, None
+    return grp, gmask[: ng.value].copy()
+
+
 def tc_selftest(n: int = 128, k: int = 64) -> float:
     """Largest absolute error of a 128 x n x k BF16 tensor-core product against the exact one."""
     err = ctypes.c_double()

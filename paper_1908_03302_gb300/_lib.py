@@ -93,6 +93,7 @@ SIGNATURES = {
     "fft_cg_load": (ctypes.c_int, [_VP, _VP, _I64, _VP]),
     "fft_psf_batch": (ctypes.c_int, [_VP, _VP, _I32, _VP, _I32, _VP, _I32, _VP, _VP]),
     "fft_psf_noalloc": (ctypes.c_int, [_VP, _I64, _VP, _I32, _VP, _VP]),
+    "fft_psf_row_groups": (ctypes.c_int, [_I64, _VP, _I32, _VP, _VP, _VP, ctypes.POINTER(_I32)]),
     "fft_tc_selftest": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_D)]),
     "fft_last_error": (ctypes.c_char_p, []),
 }

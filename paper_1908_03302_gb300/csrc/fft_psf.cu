@@ -104,6 +104,43 @@ __global__ void dsparse_kernel(const DParams D, int32_t* __restrict__ cnt, const
 
 using namespace fftgb;
 
+// Host only: rows grouped by the set of subsets that hold them (see fft_gb300.h).
+extern "C" fft_status fft_psf_row_groups(int64_t n_rows, const int32_t* subset_off, int32_t n_subsets,
+                                         const int32_t* subset_rows, uint8_t* grp, uint32_t* gmask,
+                                         int32_t* n_groups) {
+    FFT_ARG(subset_off && grp && gmask && n_groups, "fft_psf_row_groups: null argument");
+    FFT_ARG(n_rows >= 0 && n_subsets >= 1 && n_subsets <= 32, "fft_psf_row_groups: need n_rows >= 0 and 1 .. 32 subsets");
+    FFT_ARG(subset_off[0] == 0, "fft_psf_row_groups: subset_off[0] must be 0");
+    for (int s = 0; s < n_subsets; ++s)
+        FFT_ARG(subset_off[s + 1] >= subset_off[s], "fft_psf_row_groups: subset offsets must be non-decreasing");
+    FFT_ARG(subset_off[n_subsets] == 0 || subset_rows, "fft_psf_row_groups: null subset_rows");
+    std::vector<uint32_t> member((size_t)n_rows, 0u);
+    for (int s = 0; s < n_subsets; ++s)
+        for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) {
+            const int32_t p = subset_rows[i];
+            FFT_ARG(p >= 0 && p < n_rows, "fft_psf_row_groups: subset row out of range");
+            FFT_ARG(!((member[p] >> s) & 1u), "fft_psf_batch: a subset lists a row twice");
+            member[p] |= 1u << s;
+        }
+    int32_t ng = 0;
+    for (int64_t p = 0; p < n_rows; ++p) {
+        grp[p] = 0xFF;
+        if (!member[p]) continue;
+        int32_t gi = 0;
+        while (gi < ng && gmask[gi] != member[p]) ++gi;
+        if (gi == ng) {
+            if (ng == PSF_TC_MAX_GROUPS) {   // too many distinct sets for one launch
+                *n_groups = -1;
+                return FFT_OK;
+            }
+            gmask[ng++] = member[p];
+        }
+        grp[p] = (uint8_t)gi;
+    }
+    *n_groups = ng;
+    return FFT_OK;
+}
+
 namespace {
 
 // Tensor-core path for subsets whose rows fall into at most PSF_TC_MAX_GROUPS groups (rows with
@@ -194,40 +231,26 @@ fft_status psf_tc_groups(fft_geom g, const int64_t* spike_vox, int32_t n_spike, 
 // one at a time.
 fft_status psf_tc_path(fft_geom g, const int64_t* spike_vox, int32_t n_spike, const int32_t* subset_off,
                        int32_t n_subsets, const int32_t* subset_rows, float* out_dev, cudaStream_t st) {
-    std::vector<uint32_t> member(g->M, 0u);
-    for (int s = 0; s < n_subsets; ++s)
-        for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) {
-            FFT_ARG(!((member[subset_rows[i]] >> s) & 1u), "fft_psf_batch: a subset lists a row twice");
-            member[subset_rows[i]] |= 1u << s;
-        }
+    // rows listed twice are rejected here, before any device work
+    std::vector<uint8_t> grp(g->M);
+    std::vector<uint32_t> gmask(PSF_TC_MAX_GROUPS);
+    int32_t n_groups = 0;
+    fft_status rc = fft_psf_row_groups(g->M, subset_off, n_subsets, subset_rows, grp.data(), gmask.data(), &n_groups);
+    if (rc != FFT_OK) return rc;
+    const bool fits = n_groups >= 0;
+    gmask.resize(fits ? n_groups : 0);
     g->psf_tc_mma_flops = 0.0;
     g->psf_tc_entries = 0.0;
     cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(float) * (size_t)n_subsets * n_spike * g->V, st);
     if (e != cudaSuccess) return cuda_fail(e, "fft_psf_batch (tensor cores)");
-    std::vector<uint32_t> gmask;   // distinct non-empty sets, in order of first appearance
-    std::vector<uint8_t> grp(g->M, 0xFF);
-    bool fits = true;
-    for (int64_t p = 0; p < g->M && fits; ++p) {
-        if (!member[p]) continue;
-        size_t gi = 0;
-        while (gi < gmask.size() && gmask[gi] != member[p]) ++gi;
-        if (gi == gmask.size()) {
-            if ((int)gmask.size() == PSF_TC_MAX_GROUPS) {
-                fits = false;
-                break;
-            }
-            gmask.push_back(member[p]);
-        }
-        grp[p] = (uint8_t)gi;
-    }
-    if (gmask.empty()) return FFT_OK;
+    if (fits && gmask.empty()) return FFT_OK;
     if (fits) return psf_tc_groups(g, spike_vox, n_spike, n_subsets, grp, gmask, out_dev, st);
     for (int s = 0; s < n_subsets; ++s) {
         std::fill(grp.begin(), grp.end(), (uint8_t)0xFF);
         for (int32_t i = subset_off[s]; i < subset_off[s + 1]; ++i) grp[subset_rows[i]] = 0;
         if (subset_off[s + 1] == subset_off[s]) continue;
         const std::vector<uint32_t> one(1, 1u);
-        fft_status rc = psf_tc_groups(g, spike_vox, n_spike, 1, grp, one, out_dev + (int64_t)s * n_spike * g->V, st);
+        rc = psf_tc_groups(g, spike_vox, n_spike, 1, grp, one, out_dev + (int64_t)s * n_spike * g->V, st);
         if (rc != FFT_OK) return rc;
     }
     return FFT_OK;
